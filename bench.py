@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: RREF via block-iterative PLE of a dense random GF(2) matrix.
+
+One step = one gf2_rref (PLE followed by RREF recovery, every step of the
+hot path) of the 65536 x 65536 Bernoulli(1/2) matrix (512 MiB packed), the
+paper's Table 2 workload at the size the project targets.  The throughput is
+bit-operations per second with the LINPACK-style count
+W(m, n, r) = m n r - (m + n) r^2 / 2 + r^3 / 3 (= n^3/3 for a full-rank
+square matrix).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (eager elimination, all host cores) on
+a bounded sample of the same workload: the first pivot steps of the same
+matrix over its full width.  Under torchrun (N > 1) every rank runs an
+independent replica on its own GPU (the single-matrix path has no exchange
+step); the reference arm runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PLE seconds & Gbitop/s at 32768²/65536² GF(2); batched mats/s; served p99 ms"
+UNIT = "Gbitop/s"
+N_MAIN = 65536
+N_SIDE = 32768
+L2_BYTES = 126 * 2**20
+
+
+def work_bits(m: int, n: int, r: int) -> float:
+    return m * n * r - (m + n) * r * r / 2.0 + r ** 3 / 3.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def update_kernel_traffic():
+    """Per-launch DRAM traffic of the update kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_1111_6549_gb300", "csrc", "kernels_update.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "update_kernel*.md")):
+        text = open(path).read()
+        mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+        mt = re.search(r"traffic_bytes_per_launch_65536:\s*([0-9.eE+]+)", text)
+        if mh and mt and mh.group(1) == digest:
+            return float(mt.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gf2_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def oracle_sample(A: np.ndarray, m: int, n: int, pivots: int, threads: int):
+    """Time the oracle's first `pivots` elimination steps over the full width."""
+    import oracle
+    B = A.copy()
+    t0 = time.perf_counter()
+    k, _, _ = oracle.ple(B, m, n, max_pivots=pivots, threads=threads)
+    dt = time.perf_counter() - t0
+    w = sum((m - p) * (n - p) for p in range(k))
+    return w, dt, k
+
+
+def cpu_baseline(A: np.ndarray, m: int, n: int, target_s: float = 12.0):
+    threads = os.cpu_count() or 1
+    w1, dt1, k1 = oracle_sample(A, m, n, 32, threads)
+    per = dt1 / max(k1, 1)
+    piv = int(max(64, min(8192, target_s / max(per, 1e-6))))
+    w, dt, k = oracle_sample(A, m, n, piv, threads)
+    return {"value": w / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {k} pivot steps of the eager oracle elimination of the same "
+                      f"{m}x{n} matrix over its full width ({dt:.1f} s); W = sum_p (m-p)(n-p)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    import gf2inputs as gi
+    m = n = N_MAIN
+    A = gi.dense_square(n)
+    threads = os.cpu_count() or 1
+    _, dt1, k1 = oracle_sample(A, m, n, 16, threads)
+    piv = int(max(32, min(4096, 1.5 / max(dt1 / max(k1, 1), 1e-6))))   # about 1.5 s per step
+    for _ in range(args.warmup):
+        oracle_sample(A, m, n, piv, threads)
+    tw, tt = 0.0, 0.0
+    for _ in range(args.steps):
+        w, dt, k = oracle_sample(A, m, n, piv, threads)
+        tw += w
+        tt += dt
+    value = tw / tt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"rref_via_ple dense Bernoulli(1/2) {m}x{n} GF(2)", "m": m, "n": n,
+                       "sample_pivots_per_step": piv},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"first {piv} pivot steps of the eager oracle elimination of "
+                                       f"the {m}x{n} matrix over its full width, per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import gf2inputs as gi
+    import paper_1111_6549_gb300 as g
+
+    world, rank, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h = g.Handle(local)
+    stream = torch.cuda.current_stream(dev)
+
+    m = n = args.n
+    A = gi.dense_square(n)
+    W = gi.words_for(n)
+    pristine = torch.from_numpy(A.view(np.int64)).to(dev)
+    work = torch.empty_like(pristine)
+    Q = torch.empty(n, dtype=torch.int64, device=dev)
+
+    def step():
+        return h.rref_async(work, m, n, Q, rank_dev)
+
+    rank_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        work.copy_(pristine)
+        step()
+    torch.cuda.synchronize()
+    r = int(rank_dev.cpu()[0])
+
+    # ---- timed region (device time of exactly K steps)
+    h.reset_stats()
+    h.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            work.copy_(pristine)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if pg:
+        pg.barrier()
+    st = h.stats()
+    h.set_profiling(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    per_step_ms = ms / args.steps
+    max_ms = ms
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        max_ms = float(t[0])
+    W_bits = work_bits(m, n, r)
+    value = world * args.steps * W_bits / (max_ms / 1e3) / 1e9
+
+    # ---- roofline of the dominant kernel (the tabulated update), measured live
+    hbm, hbm_kind = peaks()
+    upd_gbs = st["update_bytes"] / (st["update_ms"] / 1e3) / 1e9 if st["update_ms"] > 0 else None
+    upd_per_launch_bytes = st["update_bytes"] / max(st["update_launches"], 1)
+    traffic = update_kernel_traffic()
+    roofline = {"kernel": "update_kernel (tabulated trailing update, PLE + RREF passes)",
+                "bound": "hbm", "achieved": upd_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": (upd_gbs / hbm) if upd_gbs else None, "peak_kind": hbm_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": upd_per_launch_bytes,
+                "launches_per_step": st["update_launches"] / args.steps,
+                "update_share_of_step": st["update_ms"] / ms if ms > 0 else None}
+
+    # ---- 32768^2 side measurement (same path, a few steps)
+    side = {}
+    if args.side and rank == 0:
+        ns = N_SIDE
+        As = gi.dense_square(ns)
+        ps = torch.from_numpy(As.view(np.int64)).to(dev)
+        ws = torch.empty_like(ps)
+        Qs = torch.empty(ns, dtype=torch.int64, device=dev)
+        rk = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(3):
+            ws.copy_(ps)
+            h.rref_async(ws, ns, ns, Qs, rk)
+        times = []
+        for _ in range(5):
+            ws.copy_(ps)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.rref_async(ws, ns, ns, Qs, rk)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        rs = int(rk.cpu()[0])
+        tmed = statistics.median(times)
+        # PLE alone at 32768^2
+        pt = []
+        Ps = torch.empty(ns, dtype=torch.int64, device=dev)
+        for _ in range(5):
+            ws.copy_(ps)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.ple_async(ws, ns, ns, Ps, Qs, rk)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pt.append(a.elapsed_time(b))
+        side = {"n": ns, "rank": rs, "rref_ms": tmed, "rref_gbitops": work_bits(ns, ns, rs) / tmed / 1e6,
+                "ple_ms": statistics.median(pt), "ple_gbitops": work_bits(ns, ns, rs) / statistics.median(pt) / 1e6}
+        del ps, ws
+    # PLE alone at the main size
+    ple_ms = None
+    if rank == 0:
+        P = torch.empty(n, dtype=torch.int64, device=dev)
+        pt = []
+        for _ in range(3):
+            work.copy_(pristine)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.ple_async(work, m, n, P, Q, rank_dev)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pt.append(a.elapsed_time(b))
+        ple_ms = statistics.median(pt)
+
+    # ---- end to end through the host-buffer C ABI call (pinned buffers)
+    e2e = None
+    if rank == 0 or True:
+        pin = torch.empty((m, W), dtype=torch.int64, pin_memory=True)
+        pin_src = torch.from_numpy(A.view(np.int64))
+        Qh = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        pin.copy_(pin_src)
+        h.rref_host(pin, m, n, Qh)          # warm-up
+        tt = 0.0
+        steps_e2e = max(1, min(args.steps, 5))
+        for _ in range(steps_e2e):
+            pin.copy_(pin_src)
+            t0 = time.perf_counter()
+            h.rref_host(pin, m, n, Qh)
+            tt += time.perf_counter() - t0
+        e2e = {"value": steps_e2e * W_bits / tt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": m * W * 8, "d2h_bytes_per_step": m * W * 8 + n * 8 + 8,
+               "steps": steps_e2e, "ms_per_step": tt / steps_e2e * 1e3,
+               "call": "gf2_rref_host (pinned host buffers; H2D, PLE, RREF, D2H, synchronous)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(A, m, n)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": f"rref_via_ple dense Bernoulli(1/2) {m}x{n} GF(2), 512 MiB packed",
+                           "m": m, "n": n, "rank": r, "stripe_columns": 64,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "inputs (512 MiB) larger than L2; fresh copy restored before each step",
+                           "seconds_per_step": max_ms / args.steps / 1e3,
+                           "ple_only_ms": ple_ms, "side_32768": side},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": st["kernel_launches"], "clocks": clk.summary(),
+                "panel_fallbacks": st["panel_fallbacks"], "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--no-side", dest="side", action="store_false")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * gf2.h -- C ABI of libgf2: dense linear algebra over GF(2) on one GB300 GPU.
+ *
+ * Method: block-iterative PLE decomposition (Albrecht, Bard & Pernet,
+ * "Efficient Dense Gaussian Elimination over the Finite Field with Two
+ * Elements", Section 3.2, Algorithm 2), its lazy panel elimination
+ * (Algorithm 1), the tabulated trailing update (Algorithms 5-6, "Method of
+ * the Four Russians" tables), and the RREF recovered from the PLE form
+ * (Section 5).
+ *
+ * Matrix layout (all entry points): row-major, bit-packed.  A matrix with m
+ * rows and n columns occupies m rows of ld_words uint64 words,
+ * ld_words >= ceil(n/64).  Column j of a row is bit (j % 64) of word j / 64
+ * (least significant bit = lowest column).  Bits at columns >= n (padding)
+ * must be zero on input and are zero on output.  A row start that is 16-byte
+ * aligned (ld_words even and base 16-byte aligned) takes the vectorised path.
+ *
+ * Pointers: unless stated otherwise, matrix and vector pointers are DEVICE
+ * pointers on the handle's device; scalar outputs (rank, status) are HOST
+ * pointers.  The caller owns every buffer; the handle owns its workspace.
+ *
+ * Asynchrony: work is enqueued on the handle's stream (gf2_set_stream; the
+ * default stream otherwise).  Entry points that return a host scalar (rank,
+ * solve status) synchronise that stream before returning; the _async forms
+ * write the scalar to device memory instead and do not synchronise.
+ *
+ * Errors: every call returns GF2_OK (0) or a GF2_E* code; gf2_strerror names
+ * it.  Invalid sizes or null pointers give GF2_EINVAL before any work is
+ * enqueued.  GF2_ECUDA reports a CUDA runtime error (the stream may then hold
+ * partially updated data).  m = 0 or n = 0 is valid and gives rank 0.
+ */
+#ifndef GF2_H
+#define GF2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GF2_OK        0
+#define GF2_EINVAL    1  /* bad argument: null pointer, negative size, ld too small */
+#define GF2_ENOMEM    2  /* device workspace allocation failed                     */
+#define GF2_ECUDA     3  /* CUDA runtime error                                     */
+#define GF2_ETIMEOUT  4  /* a bounded device-side wait ran out                     */
+#define GF2_EINTERNAL 5  /* internal consistency check failed on the device        */
+
+/* gf2_solve status values */
+#define GF2_SOLVE_UNIQUE          0  /* rank n: the unique solution              */
+#define GF2_SOLVE_UNDERDETERMINED 1  /* consistent, rank < n, free variables = 0 */
+#define GF2_SOLVE_INCONSISTENT    2  /* no solution; B holds no solution         */
+
+typedef struct gf2_handle *gf2_handle_t;
+
+/* Create a handle bound to CUDA device `device` (the current device when -1).
+ * The handle caches the SM count and owns a workspace grown on demand. */
+int gf2_create(gf2_handle_t *handle, int device);
+/* Free the handle and its workspace (synchronises its stream first). */
+int gf2_destroy(gf2_handle_t handle);
+/* Use `stream` (a cudaStream_t, passed as void*) for all later work. */
+int gf2_set_stream(gf2_handle_t handle, void *stream);
+
+/*
+ * PLE decomposition, in place (Section 2, Definition "PLE Decomposition";
+ * Section 3.2, Algorithm 2 "Ensures": A <- L\E, A = P L E, Q_i = column of
+ * the i-th pivot of E).
+ *   A      device, m x n, ld_words per row.  Overwritten with the
+ *          space-sharing form L\E of Section 1.2: entry (i, j) holds L[i][j]
+ *          when i > j (only columns j < rank carry L bits; L's columns >= rank
+ *          are the identity) and E[i][j] otherwise.
+ *   P      device int64[m]: LAPACK-style swap vector (Section 1.2): at step i
+ *          rows i and P[i] were exchanged; P[i] = i for i >= rank.
+ *   Q      device int64[min(m, n)]: Q[i] = column of pivot i for i < rank,
+ *          -1 after.  Pivot rule: leftmost column with a nonzero among the
+ *          remaining rows, then the first such row in the current order
+ *          (Algorithm 1), so P, Q, L and E are unique.
+ *   rank   host int64*: the rank (this call synchronises the stream).
+ */
+int gf2_ple(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
+            int64_t *P, int64_t *Q, int64_t *rank);
+/* As gf2_ple, but the rank goes to DEVICE memory rank_dev and nothing waits. */
+int gf2_ple_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
+                  int64_t *P, int64_t *Q, int64_t *rank_dev);
+
+/*
+ * Reduced row echelon form, in place (Section 2, Definition "Reduced Row
+ * Echelon Form"), computed as in Section 5: PLE first, then the RREF is
+ * recovered from E by clearing every pivot column above its pivot.
+ *   A      device, overwritten with RREF(A); rows >= rank are zero.
+ *   Q      device int64[min(m, n)]: pivot columns (the column rank profile,
+ *          Section 2), -1 past the rank.
+ *   rank   host int64* (synchronises the stream).
+ */
+int gf2_rref(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
+             int64_t *Q, int64_t *rank);
+int gf2_rref_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
+                   int64_t *Q, int64_t *rank_dev);
+
+/*
+ * Product over GF(2) by tabulated row combinations (Section 3.2: the trailing
+ * update is the M4RM multiplication of Albrecht, Bard & Hart; Algorithms 5-6).
+ *   C = A B (accumulate = 0) or C ^= A B (accumulate != 0).
+ *   A device m x k (lda words), B device k x n (ldb), C device m x n (ldc).
+ *   C must not overlap A or B.  Asynchronous.
+ */
+int gf2_mul(gf2_handle_t handle, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda,
+            const uint64_t *B, int64_t ldb, int64_t m, int64_t k, int64_t n, int accumulate);
+
+/*
+ * Solve A X = B through the PLE decomposition (Section 1: decompositions as
+ * the building block for solving dense systems; the conventions are this
+ * library's).  A device n x n (lda) is overwritten with L\E of A; B device
+ * n x nrhs (ldb) is overwritten with X when a solution exists: X[Q[p]] from
+ * back-substitution on E's pivot columns, X[j] = 0 for non-pivot columns j.
+ *   solve_status  host int*: GF2_SOLVE_UNIQUE, GF2_SOLVE_UNDERDETERMINED or
+ *                 GF2_SOLVE_INCONSISTENT (B's contents are then unspecified).
+ * Synchronises the stream.
+ */
+int gf2_solve(gf2_handle_t handle, uint64_t *A, int64_t n, int64_t lda, uint64_t *B,
+              int64_t nrhs, int64_t ldb, int *solve_status);
+
+/*
+ * Many independent PLE decompositions in one persistent launch (each as
+ * gf2_ple).  descs is a HOST array of count descriptors; A, P, Q and rank in
+ * each descriptor are DEVICE pointers (rank: one int64).  Matrices must not
+ * overlap.  Asynchronous.
+ */
+typedef struct gf2_desc {
+    uint64_t *A;
+    int64_t m, n, ld_words;
+    int64_t *P;
+    int64_t *Q;
+    int64_t *rank;
+} gf2_desc;
+int gf2_ple_batched(gf2_handle_t handle, const gf2_desc *descs, int64_t count);
+
+/* Device workspace gf2_ple / gf2_rref need for an m x n matrix, in bytes. */
+size_t gf2_workspace_bytes(gf2_handle_t handle, int64_t m, int64_t n);
+
+/*
+ * Host-buffer forms for end-to-end use: A (and P, Q) are HOST pointers
+ * (pinned memory gives the fastest copies).  Each call copies the input to
+ * the device, runs gf2_ple / gf2_rref there and copies the results back,
+ * synchronously.  Device buffers are held in the handle's workspace.
+ */
+int gf2_ple_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
+                 int64_t *P, int64_t *Q, int64_t *rank);
+int gf2_rref_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
+                  int64_t *Q, int64_t *rank);
+
+/* Counters of the work enqueued since the last reset (host struct). */
+typedef struct gf2_stats {
+    int64_t kernel_launches;      /* kernels of this library enqueued          */
+    int64_t update_launches;      /* trailing-update kernel launches           */
+    double  update_ms;            /* summed CUDA-event time of those launches
+                                     (only while profiling is on)              */
+    double  update_bytes;         /* algorithmic bytes they moved: 16 bytes per
+                                     64-bit word read and written              */
+    int64_t panel_fallbacks;      /* stripes that needed the block-wide panel  */
+} gf2_stats;
+/* Turn per-launch event timing of the update kernel on or off. */
+int gf2_set_profiling(gf2_handle_t handle, int on);
+/* Read the counters (synchronises the stream to finish the event timing). */
+int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);
+int gf2_reset_stats(gf2_handle_t handle);
+
+/* Static name of a status code. */
+const char *gf2_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF2_H */

@@ -1,0 +1,269 @@
+"""GB300 GF(2) dense elimination: thin Python binding of libgf2 (include/gf2.h).
+
+Everything computes in the CUDA library; this module only marshals
+arguments.  Matrices are torch ``int64`` tensors on the GPU holding raw
+64-bit words (row-major, column j = bit j % 64 of word j // 64, padding bits
+zero).  There is no CPU path: if the library cannot be loaded the calls raise.
+
+Entry points (same names as the C ABI, without the ``gf2_`` prefix):
+``ple``, ``ple_async``, ``rref``, ``rref_async``, ``mul``, ``solve``,
+``ple_batched``, ``ple_host``, ``rref_host``, ``workspace_bytes`` and the
+statistics helpers on :class:`Handle`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["Handle", "GF2Error", "load", "lib_path", "SOLVE_UNIQUE", "SOLVE_UNDERDETERMINED",
+           "SOLVE_INCONSISTENT", "words_for", "default_handle"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
+SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
+
+
+class GF2Error(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)}")
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("update_launches", ctypes.c_int64),
+                ("update_ms", ctypes.c_double), ("update_bytes", ctypes.c_double),
+                ("panel_fallbacks", ctypes.c_int64)]
+
+
+class Desc(ctypes.Structure):
+    """gf2_desc of the batched entry point."""
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("ld_words", ctypes.c_int64), ("P", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("rank", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    from . import build as _build
+    return _build.LIB
+
+
+def load():
+    """Load libgf2.so, building it first (nvcc, sm_103a) when it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        path = _build.LIB
+        if not _build.up_to_date():
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i64, i32p = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "gf2_create": ([ctypes.POINTER(vp), ctypes.c_int], ctypes.c_int),
+            "gf2_destroy": ([vp], ctypes.c_int),
+            "gf2_set_stream": ([vp, vp], ctypes.c_int),
+            "gf2_ple": ([vp, vp, i64, i64, i64, vp, vp, i64p], ctypes.c_int),
+            "gf2_ple_async": ([vp, vp, i64, i64, i64, vp, vp, vp], ctypes.c_int),
+            "gf2_rref": ([vp, vp, i64, i64, i64, vp, i64p], ctypes.c_int),
+            "gf2_rref_async": ([vp, vp, i64, i64, i64, vp, vp], ctypes.c_int),
+            "gf2_mul": ([vp, vp, i64, vp, i64, vp, i64, i64, i64, i64, ctypes.c_int], ctypes.c_int),
+            "gf2_solve": ([vp, vp, i64, i64, vp, i64, i64, i32p], ctypes.c_int),
+            "gf2_ple_batched": ([vp, ctypes.POINTER(Desc), i64], ctypes.c_int),
+            "gf2_workspace_bytes": ([vp, i64, i64], ctypes.c_size_t),
+            "gf2_ple_host": ([vp, vp, i64, i64, i64, vp, vp, i64p], ctypes.c_int),
+            "gf2_rref_host": ([vp, vp, i64, i64, i64, vp, i64p], ctypes.c_int),
+            "gf2_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
+            "gf2_get_stats": ([vp, ctypes.POINTER(_Stats)], ctypes.c_int),
+            "gf2_reset_stats": ([vp], ctypes.c_int),
+            "gf2_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().gf2_strerror(code).decode()
+    except Exception:  # pragma: no cover
+        return f"status {code}"
+
+
+def words_for(n: int) -> int:
+    return (n + 63) // 64
+
+
+def _check(rc: int, what: str):
+    if rc != GF2_OK:
+        raise GF2Error(rc, what)
+
+
+def _dptr(t) -> int:
+    """Device pointer of a CUDA tensor (no copy)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def _mat(t, m: int, n: int):
+    if t.dtype.itemsize != 8 or t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("matrix must be a 2-D tensor of 64-bit words with unit column stride")
+    if t.shape[0] < m or (n > 0 and t.stride(0) < words_for(n)):
+        raise ValueError("matrix too small for m x n")
+    return t.stride(0)
+
+
+class Handle:
+    """A libgf2 handle on one CUDA device, bound to torch's current stream."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        self._torch = torch
+        L = load()
+        dev = torch.cuda.current_device() if device is None else device
+        self.device = dev
+        h = ctypes.c_void_p()
+        _check(L.gf2_create(ctypes.byref(h), dev), "gf2_create")
+        self._h = h
+        self._stream = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gf2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        s = self._torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            _check(load().gf2_set_stream(self._h, ctypes.c_void_p(s)), "gf2_set_stream")
+            self._stream = s
+
+    # ---- decompositions ------------------------------------------------
+    def ple(self, A, m: int, n: int, P, Q) -> int:
+        """PLE in place; P int64[m], Q int64[min(m,n)] device tensors.  Returns the rank."""
+        ld = _mat(A, m, n)
+        self._bind_stream()
+        rank = ctypes.c_int64(0)
+        _check(load().gf2_ple(self._h, _dptr(A), m, n, ld, _dptr(P), _dptr(Q), ctypes.byref(rank)),
+               "gf2_ple")
+        return rank.value
+
+    def ple_async(self, A, m: int, n: int, P, Q, rank_dev) -> None:
+        ld = _mat(A, m, n)
+        self._bind_stream()
+        _check(load().gf2_ple_async(self._h, _dptr(A), m, n, ld, _dptr(P), _dptr(Q), _dptr(rank_dev)),
+               "gf2_ple_async")
+
+    def rref(self, A, m: int, n: int, Q) -> int:
+        ld = _mat(A, m, n)
+        self._bind_stream()
+        rank = ctypes.c_int64(0)
+        _check(load().gf2_rref(self._h, _dptr(A), m, n, ld, _dptr(Q), ctypes.byref(rank)), "gf2_rref")
+        return rank.value
+
+    def rref_async(self, A, m: int, n: int, Q, rank_dev) -> None:
+        ld = _mat(A, m, n)
+        self._bind_stream()
+        _check(load().gf2_rref_async(self._h, _dptr(A), m, n, ld, _dptr(Q), _dptr(rank_dev)),
+               "gf2_rref_async")
+
+    def mul(self, C, A, B, m: int, k: int, n: int, accumulate: bool = False) -> None:
+        ldc = _mat(C, m, n)
+        lda = A.stride(0) if k > 0 else 1
+        ldb = B.stride(0) if k > 0 else 1
+        self._bind_stream()
+        _check(load().gf2_mul(self._h, _dptr(C), ldc, _dptr(A) if k else None, lda,
+                              _dptr(B) if k else None, ldb, m, k, n, 1 if accumulate else 0), "gf2_mul")
+
+    def solve(self, A, B, n: int, nrhs: int) -> int:
+        lda = _mat(A, n, n)
+        ldb = _mat(B, n, nrhs) if nrhs > 0 else 1
+        self._bind_stream()
+        st = ctypes.c_int(0)
+        _check(load().gf2_solve(self._h, _dptr(A), n, lda, _dptr(B) if nrhs else None, nrhs, ldb,
+                                ctypes.byref(st)), "gf2_solve")
+        return st.value
+
+    def ple_batched(self, items) -> None:
+        """items: sequence of (A, m, n, P, Q, rank_dev) device tensors / sizes."""
+        arr = (Desc * len(items))()
+        for i, (A, m, n, P, Q, rk) in enumerate(items):
+            ld = _mat(A, m, n)
+            arr[i] = Desc(_dptr(A), m, n, ld, _dptr(P), _dptr(Q), _dptr(rk))
+        self._bind_stream()
+        _check(load().gf2_ple_batched(self._h, arr, len(items)), "gf2_ple_batched")
+
+    def workspace_bytes(self, m: int, n: int) -> int:
+        return int(load().gf2_workspace_bytes(self._h, m, n))
+
+    # ---- host-buffer forms ----------------------------------------------
+    def ple_host(self, A: np.ndarray, m: int, n: int):
+        """PLE of a host uint64 array in place; returns (rank, P, Q) as numpy."""
+        assert A.dtype == np.uint64 and A.flags["C_CONTIGUOUS"]
+        P = np.zeros(max(m, 1), dtype=np.int64)
+        Q = np.zeros(max(min(m, n), 1), dtype=np.int64)
+        rank = ctypes.c_int64(0)
+        self._bind_stream()
+        _check(load().gf2_ple_host(self._h, A.ctypes.data, m, n, A.shape[1], P.ctypes.data,
+                                   Q.ctypes.data, ctypes.byref(rank)), "gf2_ple_host")
+        return rank.value, P[:m], Q[:min(m, n)]
+
+    def rref_host(self, A, m: int, n: int, Q=None) -> int:
+        """RREF of a host buffer in place.  A: numpy uint64 array or a pinned
+        CPU torch tensor of 64-bit words; Q likewise (int64[min(m, n)])."""
+        if isinstance(A, np.ndarray):
+            aptr, ld = A.ctypes.data, A.shape[1]
+        else:
+            aptr, ld = A.data_ptr(), A.stride(0)
+        if Q is None:
+            Q = np.zeros(max(min(m, n), 1), dtype=np.int64)
+        qptr = Q.ctypes.data if isinstance(Q, np.ndarray) else Q.data_ptr()
+        rank = ctypes.c_int64(0)
+        self._bind_stream()
+        _check(load().gf2_rref_host(self._h, aptr, m, n, ld, qptr, ctypes.byref(rank)), "gf2_rref_host")
+        return rank.value
+
+    # ---- statistics -----------------------------------------------------
+    def set_profiling(self, on: bool) -> None:
+        _check(load().gf2_set_profiling(self._h, 1 if on else 0), "gf2_set_profiling")
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(load().gf2_get_stats(self._h, ctypes.byref(s)), "gf2_get_stats")
+        return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+    def reset_stats(self) -> None:
+        _check(load().gf2_reset_stats(self._h), "gf2_reset_stats")
+
+
+_default = {}
+
+
+def default_handle(device: int | None = None) -> Handle:
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    h = _default.get(dev)
+    if h is None:
+        h = _default[dev] = Handle(dev)
+    return h

@@ -1,0 +1,625 @@
+// api.cu -- host orchestration and the C ABI declared in include/gf2.h.
+//
+// Block-iterative PLE (Section 3.2, Algorithm 2): the host enqueues, per
+// 64-column stripe, the panel (pivot search), the prep (L bits and table
+// indices) and the trailing update, all on the handle's stream with no host
+// synchronisation in between; the running rank lives in device memory, so
+// the stripe loop needs no round trip.  RREF recovery (Section 5) walks the
+// stripes backwards with the same update kernel.  Solve runs the same PLE on
+// the augmented matrix [A | B] with pivots restricted to A's columns.
+#include "common.cuh"
+#include "gf2.h"
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+using namespace gf2;
+
+struct gf2_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    char *ws = nullptr;        // stripe records, indices, staged rows, panel scratch
+    size_t ws_cap = 0;
+    char *io = nullptr;        // host-API device copies, solve's augmented matrix
+    size_t io_cap = 0;
+    char *small = nullptr;     // rank, flags, counters
+    int64_t launches = 0;
+    int64_t upd_launches = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    double upd_ms = 0.0;
+};
+
+namespace {
+
+// layout of the small device block
+constexpr size_t SM_RANK = 0;      // int64 running rank
+constexpr size_t SM_ERR = 8;       // int32 internal-check flag
+constexpr size_t SM_FALLBACK = 12; // int32 block-wide panel count
+constexpr size_t SM_BYTES = 16;    // uint64 algorithmic bytes of update launches
+constexpr size_t SM_FLAG = 24;     // int32 solve inconsistency flag
+constexpr size_t SM_BYTES_TOTAL = 256;
+
+int64_t *r_dev(gf2_handle *h) { return reinterpret_cast<int64_t *>(h->small + SM_RANK); }
+int32_t *err_dev(gf2_handle *h) { return reinterpret_cast<int32_t *>(h->small + SM_ERR); }
+int32_t *fb_dev(gf2_handle *h) { return reinterpret_cast<int32_t *>(h->small + SM_FALLBACK); }
+unsigned long long *bytes_dev(gf2_handle *h)
+{
+    return reinterpret_cast<unsigned long long *>(h->small + SM_BYTES);
+}
+int32_t *flag_dev(gf2_handle *h) { return reinterpret_cast<int32_t *>(h->small + SM_FLAG); }
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int64_t words_for(int64_t n) { return (n + 63) >> 6; }
+
+struct Layout {
+    size_t descs, idx, map, S, gval, glb, gsrc, P, Q, total;
+    int64_t ldS;
+};
+
+Layout layout_for(int64_t m, int64_t ncols)
+{
+    Layout L{};
+    const int64_t ns = std::max<int64_t>(words_for(ncols), 1);
+    const int64_t W = std::max<int64_t>(words_for(ncols), 1);
+    const int64_t mm = std::max<int64_t>(m, 1);
+    L.ldS = W + (W & 1);
+    size_t off = 0;
+    L.descs = off; off = align256(off + (size_t)ns * sizeof(StripeDesc));
+    L.idx = off;   off = align256(off + (size_t)mm * 8);
+    L.map = off;   off = align256(off + (size_t)mm * 4);
+    L.S = off;     off = align256(off + (size_t)SMAX * L.ldS * 8);
+    L.gval = off;  off = align256(off + (size_t)mm * 8);
+    L.glb = off;   off = align256(off + (size_t)mm * 8);
+    L.gsrc = off;  off = align256(off + (size_t)mm * 4);
+    L.P = off;     off = align256(off + (size_t)mm * 8);
+    L.Q = off;     off = align256(off + (size_t)std::max<int64_t>(std::min(m, ncols), 1) * 8);
+    L.total = off;
+    return L;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int grow(char **buf, size_t *cap, size_t need, cudaStream_t st)
+{
+    if (*cap >= need) return GF2_OK;
+    if (*buf) {
+        cudaStreamSynchronize(st);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    size_t want = need + need / 4;
+    if (cudaMalloc(reinterpret_cast<void **>(buf), want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(reinterpret_cast<void **>(buf), need) != cudaSuccess) {
+            cudaGetLastError();
+            *buf = nullptr;
+            return GF2_ENOMEM;
+        }
+        want = need;
+    }
+    *cap = want;
+    return GF2_OK;
+}
+
+#define CK(expr)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (expr);                                  \
+        if (e_ != cudaSuccess) { cudaGetLastError(); return GF2_ECUDA; } \
+    } while (0)
+
+int launch_update_counted(gf2_handle *h, const UpdArgs &a)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profiling) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            if (!h->ev_free.empty()) { e = h->ev_free.back(); h->ev_free.pop_back(); }
+            else CK(cudaEventCreate(&e));
+            (i == 0 ? e0 : e1) = e;
+        }
+        CK(cudaEventRecord(e0, h->stream));
+    }
+    CK(launch_update(h->stream, a, h->num_sms));
+    if (h->profiling) {
+        CK(cudaEventRecord(e1, h->stream));
+        h->ev_pending.emplace_back(e0, e1);
+    }
+    h->launches += 1;
+    h->upd_launches += 1;
+    return GF2_OK;
+}
+
+// Enqueue the block-iterative PLE of A (m x ncols, pivots among the first
+// npiv columns).  The rank is left in r_dev.
+int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv,
+            int64_t *P, int64_t *Q)
+{
+    const Layout L = layout_for(m, ncols);
+    int rc = grow(&h->ws, &h->ws_cap, L.total, h->stream);
+    if (rc) return rc;
+    char *ws = h->ws;
+    StripeDesc *descs = reinterpret_cast<StripeDesc *>(ws + L.descs);
+    uint64_t *IDX = reinterpret_cast<uint64_t *>(ws + L.idx);
+    int32_t *map = reinterpret_cast<int32_t *>(ws + L.map);
+    uint64_t *S = reinterpret_cast<uint64_t *>(ws + L.S);
+    PanelScratch gs{reinterpret_cast<uint64_t *>(ws + L.gval), reinterpret_cast<uint64_t *>(ws + L.glb),
+                    reinterpret_cast<int32_t *>(ws + L.gsrc)};
+    const int64_t qn = std::min(m, npiv);
+    const int64_t W = words_for(ncols);
+    const int64_t ns = words_for(npiv);
+    CK(launch_init_ple(h->stream, P, Q, m, qn, map, r_dev(h), h->num_sms));
+    h->launches += 1;
+    for (int64_t s = 0; s < ns; ++s) {
+        CK(launch_panel(h->stream, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map, gs, fb_dev(h)));
+        CK(launch_prep(h->stream, A, m, ld, W, (int)s, descs, map, S, L.ldS, IDX, err_dev(h),
+                       h->num_sms));
+        h->launches += 2;
+        UpdArgs a{};
+        a.mode = UPD_PLE;
+        a.A = A;
+        a.ld = ld;
+        a.m = m;
+        a.W = W;
+        a.desc = descs + s;
+        a.stripe = (int)s;
+        a.S = S;
+        a.ldS = L.ldS;
+        a.map = map;
+        a.idx = IDX;
+        a.idx_stride = 1;
+        a.bytes = bytes_dev(h);
+        rc = launch_update_counted(h, a);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+// Enqueue the RREF recovery of a matrix that run_ple just decomposed.
+int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv)
+{
+    const Layout L = layout_for(m, ncols);
+    StripeDesc *descs = reinterpret_cast<StripeDesc *>(h->ws + L.descs);
+    uint64_t *IDX = reinterpret_cast<uint64_t *>(h->ws + L.idx);
+    const int64_t W = words_for(ncols);
+    const int64_t ns = words_for(npiv);
+    CK(launch_rref_lclear(h->stream, A, m, W, ld, r_dev(h), h->num_sms));
+    h->launches += 1;
+    for (int64_t s = ns - 1; s >= 0; --s) {
+        CK(launch_rref_prep(h->stream, A, ld, W, (int)s, descs, IDX, m, h->num_sms));
+        h->launches += 1;
+        UpdArgs a{};
+        a.mode = UPD_RREF;
+        a.A = A;
+        a.ld = ld;
+        a.m = m;
+        a.W = W;
+        a.desc = descs + s;
+        a.stripe = (int)s;
+        a.idx = IDX;
+        a.idx_stride = 1;
+        a.bytes = bytes_dev(h);
+        int rc = launch_update_counted(h, a);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+int check_args(gf2_handle *h, const void *A, int64_t m, int64_t n, int64_t ld)
+{
+    if (!h) return GF2_EINVAL;
+    if (m < 0 || n < 0) return GF2_EINVAL;
+    if (m > 0 && n > 0) {
+        if (!A) return GF2_EINVAL;
+        if (ld < words_for(n)) return GF2_EINVAL;
+    }
+    if (m >= (int64_t(1) << 31)) return GF2_EINVAL;   // slot indices are 32-bit
+    return GF2_OK;
+}
+
+int finish_sync(gf2_handle *h)
+{
+    CK(cudaStreamSynchronize(h->stream));
+    int32_t err = 0;
+    CK(cudaMemcpy(&err, err_dev(h), sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        int32_t zero = 0;
+        cudaMemcpy(err_dev(h), &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        return GF2_EINTERNAL;
+    }
+    return GF2_OK;
+}
+
+int ple_impl(gf2_handle *h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *P, int64_t *Q)
+{
+    if (m == 0) return GF2_OK;
+    if (n == 0) {
+        CK(launch_init_ple(h->stream, P, Q, m, 0, nullptr, r_dev(h),
+                           h->num_sms));
+        return GF2_OK;
+    }
+    return run_ple(h, A, m, n, ld, n, P, Q);
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int gf2_create(gf2_handle_t *handle, int device)
+{
+    if (!handle) return GF2_EINVAL;
+    *handle = nullptr;
+    int dev = device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return GF2_ECUDA;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || dev >= count) { cudaGetLastError(); return GF2_ECUDA; }
+    DeviceGuard g(dev);
+    gf2_handle *h = new (std::nothrow) gf2_handle();
+    if (!h) return GF2_ENOMEM;
+    h->device = dev;
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete h;
+        return GF2_ECUDA;
+    }
+    if (setup_update_kernel() != cudaSuccess) { cudaGetLastError(); delete h; return GF2_ECUDA; }
+    if (cudaMalloc(reinterpret_cast<void **>(&h->small), SM_BYTES_TOTAL) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return GF2_ENOMEM;
+    }
+    cudaMemset(h->small, 0, SM_BYTES_TOTAL);
+    *handle = h;
+    return GF2_OK;
+}
+
+int gf2_destroy(gf2_handle_t h)
+{
+    if (!h) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto &p : h->ev_pending) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    for (auto e : h->ev_free) cudaEventDestroy(e);
+    cudaFree(h->ws);
+    cudaFree(h->io);
+    cudaFree(h->small);
+    delete h;
+    return GF2_OK;
+}
+
+int gf2_set_stream(gf2_handle_t h, void *stream)
+{
+    if (!h) return GF2_EINVAL;
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    return GF2_OK;
+}
+
+size_t gf2_workspace_bytes(gf2_handle_t h, int64_t m, int64_t n)
+{
+    (void)h;
+    if (m <= 0 || n <= 0) return 0;
+    return layout_for(m, n).total;
+}
+
+int gf2_ple_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *P,
+                  int64_t *Q, int64_t *rank_dev)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (m > 0 && !P) return GF2_EINVAL;
+    if (m > 0 && n > 0 && !Q) return GF2_EINVAL;
+    if (!rank_dev) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    if (m == 0 || n == 0) {
+        if (m > 0) CK(launch_init_ple(h->stream, P, Q, m, 0, nullptr, r_dev(h), h->num_sms));
+        else CK(cudaMemsetAsync(r_dev(h), 0, 8, h->stream));
+    } else {
+        rc = ple_impl(h, A, m, n, ld, P, Q);
+        if (rc) return rc;
+    }
+    CK(launch_copy_rank(h->stream, r_dev(h), rank_dev));
+    h->launches += 1;
+    return GF2_OK;
+}
+
+int gf2_ple(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *P, int64_t *Q,
+            int64_t *rank)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (!rank || (m > 0 && !P) || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    *rank = 0;
+    if (m == 0) return GF2_OK;
+    if (n == 0) {
+        CK(launch_init_ple(h->stream, P, Q, m, 0, nullptr, r_dev(h), h->num_sms));
+        h->launches += 1;
+        return finish_sync(h);
+    }
+    rc = run_ple(h, A, m, n, ld, n, P, Q);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(rank, r_dev(h), sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    return finish_sync(h);
+}
+
+static int rref_enqueue(gf2_handle *h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q)
+{
+    const Layout L = layout_for(m, n);
+    int rc = grow(&h->ws, &h->ws_cap, L.total, h->stream);
+    if (rc) return rc;
+    int64_t *P = reinterpret_cast<int64_t *>(h->ws + L.P);
+    rc = run_ple(h, A, m, n, ld, n, P, Q);
+    if (rc) return rc;
+    return run_rref_back(h, A, m, n, ld, n);
+}
+
+int gf2_rref(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q, int64_t *rank)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (!rank || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    *rank = 0;
+    if (m == 0 || n == 0) return GF2_OK;
+    rc = rref_enqueue(h, A, m, n, ld, Q);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(rank, r_dev(h), sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    return finish_sync(h);
+}
+
+int gf2_rref_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q,
+                   int64_t *rank_dev)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (!rank_dev || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    if (m == 0 || n == 0) {
+        CK(cudaMemsetAsync(rank_dev, 0, 8, h->stream));
+        return GF2_OK;
+    }
+    rc = rref_enqueue(h, A, m, n, ld, Q);
+    if (rc) return rc;
+    CK(launch_copy_rank(h->stream, r_dev(h), rank_dev));
+    h->launches += 1;
+    return GF2_OK;
+}
+
+int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
+            int64_t ldb, int64_t m, int64_t k, int64_t n, int accumulate)
+{
+    if (!h || m < 0 || k < 0 || n < 0) return GF2_EINVAL;
+    if (m == 0 || n == 0) return GF2_OK;
+    if (!C || ldc < words_for(n)) return GF2_EINVAL;
+    if (k > 0 && (!A || !B || lda < words_for(k) || ldb < words_for(n))) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    const int64_t Wc = words_for(n);
+    if (!accumulate)
+        CK(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)Wc * 8, (size_t)m, h->stream));
+    for (int64_t kc = 0; kc < words_for(k); ++kc) {
+        UpdArgs a{};
+        a.mode = UPD_MUL;
+        a.A = C;
+        a.ld = ldc;
+        a.m = m;
+        a.W = Wc;
+        a.idx = A + kc;
+        a.idx_stride = lda;
+        a.B = B + kc * 64 * ldb;
+        a.ldb = ldb;
+        a.gen_count = std::min<int64_t>(64, k - 64 * kc);
+        a.row_lo = 0;
+        a.row_hi = m;
+        a.w_lo = 0;
+        a.bytes = bytes_dev(h);
+        int rc = launch_update_counted(h, a);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+int gf2_solve(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, int64_t nrhs, int64_t ldb,
+              int *solve_status)
+{
+    int rc = check_args(h, A, n, n, lda);
+    if (rc) return rc;
+    if (!solve_status || nrhs < 0) return GF2_EINVAL;
+    if (n > 0 && nrhs > 0 && (!B || ldb < words_for(nrhs))) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    *solve_status = GF2_SOLVE_UNIQUE;
+    if (n == 0) return GF2_OK;
+    const int64_t wa = words_for(n);
+    const int64_t wb = std::max<int64_t>(words_for(nrhs), 1);
+    int64_t ldaug = wa + wb;
+    ldaug += ldaug & 1;
+    const int64_t ncols = 64 * (wa + wb);
+    const size_t aug_bytes = align256((size_t)n * ldaug * 8);
+    rc = grow(&h->io, &h->io_cap, aug_bytes, h->stream);
+    if (rc) return rc;
+    const Layout L = layout_for(n, ncols);
+    rc = grow(&h->ws, &h->ws_cap, L.total, h->stream);
+    if (rc) return rc;
+    uint64_t *Aug = reinterpret_cast<uint64_t *>(h->io);
+    int64_t *P = reinterpret_cast<int64_t *>(h->ws + L.P);
+    int64_t *Q = reinterpret_cast<int64_t *>(h->ws + L.Q);
+    CK(cudaMemsetAsync(Aug, 0, (size_t)n * ldaug * 8, h->stream));
+    CK(cudaMemcpy2DAsync(Aug, (size_t)ldaug * 8, A, (size_t)lda * 8, (size_t)wa * 8, (size_t)n,
+                         cudaMemcpyDeviceToDevice, h->stream));
+    if (nrhs > 0)
+        CK(cudaMemcpy2DAsync(Aug + wa, (size_t)ldaug * 8, B, (size_t)ldb * 8, (size_t)words_for(nrhs) * 8,
+                             (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+    rc = run_ple(h, Aug, n, ncols, ldaug, n, P, Q);
+    if (rc) return rc;
+    CK(cudaMemcpy2DAsync(A, (size_t)lda * 8, Aug, (size_t)ldaug * 8, (size_t)wa * 8, (size_t)n,
+                         cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemsetAsync(flag_dev(h), 0, 4, h->stream));
+    CK(launch_solve_check(h->stream, Aug, ldaug, n, wa, wb, r_dev(h), flag_dev(h)));
+    h->launches += 1;
+    rc = run_rref_back(h, Aug, n, ncols, ldaug, n);
+    if (rc) return rc;
+    if (nrhs > 0) {
+        CK(launch_solve_finish(h->stream, Aug, ldaug, n, wa, words_for(nrhs), r_dev(h), Q, B, ldb));
+        h->launches += 2;
+    }
+    int64_t rank = 0;
+    int32_t flag = 0;
+    CK(cudaMemcpyAsync(&rank, r_dev(h), 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&flag, flag_dev(h), 4, cudaMemcpyDeviceToHost, h->stream));
+    rc = finish_sync(h);
+    if (rc) return rc;
+    *solve_status = flag ? GF2_SOLVE_INCONSISTENT : (rank == n ? GF2_SOLVE_UNIQUE : GF2_SOLVE_UNDERDETERMINED);
+    return GF2_OK;
+}
+
+int gf2_ple_batched(gf2_handle_t h, const gf2_desc *descs, int64_t count)
+{
+    if (!h || count < 0 || (count > 0 && !descs)) return GF2_EINVAL;
+    for (int64_t b = 0; b < count; ++b) {
+        const gf2_desc &d = descs[b];
+        int rc = check_args(h, d.A, d.m, d.n, d.ld_words);
+        if (rc) return rc;
+        if (!d.rank || (d.m > 0 && !d.P) || (d.m > 0 && d.n > 0 && !d.Q)) return GF2_EINVAL;
+    }
+    DeviceGuard g(h->device);
+    for (int64_t b = 0; b < count; ++b) {
+        const gf2_desc &d = descs[b];
+        int rc = gf2_ple_async(h, d.A, d.m, d.n, d.ld_words, d.P, d.Q, d.rank);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+int gf2_ple_host(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *P, int64_t *Q,
+                 int64_t *rank)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (!rank || (m > 0 && !P) || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    *rank = 0;
+    if (m == 0) return GF2_OK;
+    const int64_t qn = std::min(m, n);
+    const size_t abytes = align256((size_t)m * ld * 8);
+    const size_t pbytes = align256((size_t)m * 8);
+    const size_t need = abytes + pbytes + align256((size_t)std::max<int64_t>(qn, 1) * 8);
+    rc = grow(&h->io, &h->io_cap, need, h->stream);
+    if (rc) return rc;
+    uint64_t *dA = reinterpret_cast<uint64_t *>(h->io);
+    int64_t *dP = reinterpret_cast<int64_t *>(h->io + abytes);
+    int64_t *dQ = reinterpret_cast<int64_t *>(h->io + abytes + pbytes);
+    if (n > 0) CK(cudaMemcpyAsync(dA, A, (size_t)m * ld * 8, cudaMemcpyHostToDevice, h->stream));
+    if (n == 0) {
+        CK(launch_init_ple(h->stream, dP, dQ, m, 0, nullptr, r_dev(h), h->num_sms));
+    } else {
+        rc = run_ple(h, dA, m, n, ld, n, dP, dQ);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(A, dA, (size_t)m * ld * 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(Q, dQ, (size_t)qn * 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(rank, r_dev(h), 8, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaMemcpyAsync(P, dP, (size_t)m * 8, cudaMemcpyDeviceToHost, h->stream));
+    return finish_sync(h);
+}
+
+int gf2_rref_host(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q, int64_t *rank)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (!rank || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    *rank = 0;
+    if (m == 0 || n == 0) return GF2_OK;
+    const int64_t qn = std::min(m, n);
+    const size_t abytes = align256((size_t)m * ld * 8);
+    const size_t need = abytes + align256((size_t)qn * 8);
+    rc = grow(&h->io, &h->io_cap, need, h->stream);
+    if (rc) return rc;
+    uint64_t *dA = reinterpret_cast<uint64_t *>(h->io);
+    int64_t *dQ = reinterpret_cast<int64_t *>(h->io + abytes);
+    CK(cudaMemcpyAsync(dA, A, (size_t)m * ld * 8, cudaMemcpyHostToDevice, h->stream));
+    rc = rref_enqueue(h, dA, m, n, ld, dQ);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(A, dA, (size_t)m * ld * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(Q, dQ, (size_t)qn * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(rank, r_dev(h), 8, cudaMemcpyDeviceToHost, h->stream));
+    return finish_sync(h);
+}
+
+int gf2_set_profiling(gf2_handle_t h, int on)
+{
+    if (!h) return GF2_EINVAL;
+    h->profiling = on != 0;
+    return GF2_OK;
+}
+
+int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
+{
+    if (!h || !out) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &p : h->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) h->upd_ms += ms;
+        else cudaGetLastError();
+        h->ev_free.push_back(p.first);
+        h->ev_free.push_back(p.second);
+    }
+    h->ev_pending.clear();
+    unsigned long long bytes = 0;
+    int32_t fb = 0;
+    CK(cudaMemcpy(&bytes, bytes_dev(h), 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&fb, fb_dev(h), 4, cudaMemcpyDeviceToHost));
+    out->kernel_launches = h->launches;
+    out->update_launches = h->upd_launches;
+    out->update_ms = h->upd_ms;
+    out->update_bytes = (double)bytes;
+    out->panel_fallbacks = fb;
+    return GF2_OK;
+}
+
+int gf2_reset_stats(gf2_handle_t h)
+{
+    if (!h) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &p : h->ev_pending) { h->ev_free.push_back(p.first); h->ev_free.push_back(p.second); }
+    h->ev_pending.clear();
+    h->launches = 0;
+    h->upd_launches = 0;
+    h->upd_ms = 0.0;
+    CK(cudaMemset(h->small + SM_FALLBACK, 0, 12));
+    return GF2_OK;
+}
+
+const char *gf2_strerror(int code)
+{
+    switch (code) {
+    case GF2_OK: return "GF2_OK";
+    case GF2_EINVAL: return "GF2_EINVAL: invalid argument";
+    case GF2_ENOMEM: return "GF2_ENOMEM: device allocation failed";
+    case GF2_ECUDA: return "GF2_ECUDA: CUDA runtime error";
+    case GF2_ETIMEOUT: return "GF2_ETIMEOUT: bounded device wait ran out";
+    case GF2_EINTERNAL: return "GF2_EINTERNAL: device-side consistency check failed";
+    default: return "GF2: unknown status";
+    }
+}
+
+}  // extern "C"

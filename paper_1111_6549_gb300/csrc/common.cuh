@@ -1,0 +1,95 @@
+// common.cuh -- shared definitions of the sm_103a GF(2) elimination kernels.
+//
+// Data layout: row-major bit-packed matrices, column j = bit (j % 64) of
+// word j / 64.  The block-iterative PLE (Algorithm 2) walks the columns in
+// stripes of KS = 64 columns (one word per row), so every stripe starts on a
+// word boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gf2 {
+
+constexpr int KS = 64;            // stripe width in columns (one uint64 word)
+constexpr int SMAX = 2 * KS;      // rows staged per stripe: pivot rows + displaced rows
+constexpr int TW = 8;             // update tile width in words (64 bytes per row)
+constexpr int NTAB = KS / 8;      // 8-bit tables per stripe
+constexpr int TAB_LINE = 2 * TW;  // words per shared-memory line (two tables interleaved)
+constexpr int TAB_WORDS = (NTAB / 2) * 256 * TAB_LINE;  // 16384 words = 128 KiB
+constexpr int UPD_THREADS = 512;
+constexpr int UPD_ROWS_PER_THREAD = 4;
+constexpr int PANEL_THREADS = 512;
+constexpr int PANEL_G = 8;        // fast panel window: 32 * PANEL_G rows in one warp
+
+// Per-stripe record written by the panel kernel and read by the later
+// kernels of the stripe (and by the RREF recovery).
+struct StripeDesc {
+    int64_t r;          // rank before this stripe (first row position of the stripe)
+    int32_t rbar;       // pivots found in the stripe
+    int32_t c;          // first column of the stripe
+    int32_t nS;         // staged rows: [0, rbar) pivot rows, then displaced rows
+    int32_t maxpos;     // largest position offset (from r) of a staged row
+    int32_t tier;       // 1: warp window path, 2: block-wide path
+    int32_t pad;
+    uint64_t E11[KS];   // pivot rows' stripe word after elimination (echelon)
+    uint64_t L11[KS];   // L coefficients of pivot rows w.r.t. earlier pivots (bit q < p)
+    uint64_t Linv[KS];  // rows of L11^-1 (unit lower triangular)
+    int32_t S_off[SMAX];  // staged row k -> position offset from r
+    int64_t S_src[SMAX];  // staged row k -> physical row copied from
+    uint8_t qbar[KS];     // pivot column offsets inside the stripe
+};
+
+// Scratch of the block-wide panel path: one entry per remaining row.
+struct PanelScratch {
+    uint64_t *val;   // stripe word, eliminated eagerly
+    uint64_t *lb;    // L coefficient bits
+    int32_t *src;    // row offset (from r) whose content sits in this slot
+};
+
+enum UpdMode { UPD_PLE = 0, UPD_RREF = 1, UPD_MUL = 2 };
+
+struct UpdArgs {
+    int mode;
+    uint64_t *A;               // destination rows (and default source)
+    int64_t ld;
+    int64_t m;                 // PLE/RREF: rows of A
+    int64_t W;                 // words per row to process (exclusive upper bound)
+    const StripeDesc *desc;    // PLE/RREF: the stripe record
+    int stripe;
+    const uint64_t *S;         // PLE: staged rows
+    int64_t ldS;
+    const int32_t *map;        // PLE: position -> stripe * 256 + staged slot, or -1
+    const uint64_t *idx;       // table index per row (row i at idx[i * idx_stride])
+    int64_t idx_stride;
+    const uint64_t *B;         // MUL: generator rows B + g * ldb
+    int64_t ldb;
+    int64_t gen_count;         // MUL: number of generator rows (<= 64)
+    int64_t row_lo, row_hi;    // MUL: rows to update
+    int64_t w_lo;              // MUL: first word to update
+    unsigned long long *bytes; // algorithmic bytes counter (may be null)
+};
+
+// ---- launchers (host side, defined in the .cu files) ----
+cudaError_t launch_init_ple(cudaStream_t st, int64_t *P, int64_t *Q, int64_t m, int64_t qn,
+                            int32_t *map, int64_t *r_dev, int num_sms);
+cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t npiv, int s,
+                         StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
+                         PanelScratch gs, int32_t *fallbacks);
+cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
+                        const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
+                        uint64_t *IDX, int32_t *err, int num_sms);
+cudaError_t setup_update_kernel();
+cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
+cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t W, int64_t ld,
+                               const int64_t *r_dev, int num_sms);
+cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
+                             const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
+cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
+cudaError_t launch_solve_check(cudaStream_t st, const uint64_t *Aug, int64_t ldaug, int64_t n,
+                               int64_t wa, int64_t wb, const int64_t *r_dev, int32_t *flag);
+cudaError_t launch_solve_finish(cudaStream_t st, const uint64_t *Aug, int64_t ldaug, int64_t n,
+                                int64_t wa, int64_t wb, const int64_t *r_dev, const int64_t *Q,
+                                uint64_t *B, int64_t ldb);
+
+}  // namespace gf2

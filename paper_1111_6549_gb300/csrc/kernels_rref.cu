@@ -1,0 +1,190 @@
+// kernels_rref.cu -- RREF recovery from the PLE form, and solve helpers.
+//
+// Section 5 computes the RREF by first computing the PLE decomposition and
+// then recovering the reduced form from it (the recovery is not spelled out).
+// Here: drop L (every row keeps only its columns >= its own index; rows past
+// the rank become zero), then walk the pivot blocks of the PLE stripes from
+// the last to the first.  For block s (rows r_s .. r_s+rbar-1, pivot columns
+// inside [c_s, c_s+64)):
+//   1. reduce the block against itself: rows <- U11^-1 rows, U11 = the block
+//      restricted to its pivot columns (unit upper triangular), so each
+//      pivot column becomes a unit vector inside the block;
+//   2. clear the block's pivot columns in every row above the block with the
+//      tabulated update (kernels_update.cu, UPD_RREF), indexed by the row's
+//      stripe word, which rref_prep copies out before the update starts.
+// Later blocks only touch columns >= c_s + 64, so the stripe word of block s
+// still equals the E11 recorded by the panel when block s is processed.
+#include "common.cuh"
+
+namespace gf2 {
+
+__global__ void rref_lclear_kernel(uint64_t *A, int64_t m, int64_t W, int64_t ld, const int64_t *r_dev)
+{
+    const int64_t r = *r_dev;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp0; i < m; i += nwarps) {
+        uint64_t *row = A + i * ld;
+        if (i < r) {
+            const int64_t wl = i >> 6;
+            for (int64_t w = lane; w < wl; w += 32) row[w] = 0;
+            if (lane == 0 && (i & 63)) row[wl] &= ~((1ull << (i & 63)) - 1ull);
+        } else {
+            for (int64_t w = lane; w < W; w += 32) row[w] = 0;
+        }
+    }
+}
+
+cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t W, int64_t ld,
+                               const int64_t *r_dev, int num_sms)
+{
+    int64_t blocks = (m * 32 + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 8 * num_sms) blocks = 8 * num_sms;
+    rref_lclear_kernel<<<(int)blocks, 256, 0, st>>>(A, m, W, ld, r_dev);
+    return cudaGetLastError();
+}
+
+constexpr int RPREP_THREADS = 256;
+
+__global__ void __launch_bounds__(RPREP_THREADS)
+rref_prep_kernel(uint64_t *A, int64_t ld, int64_t W, int s, const StripeDesc *descs, uint64_t *IDX,
+                 int nbr)
+{
+    const StripeDesc *d = descs + s;
+    const int rbar = d->rbar;
+    if (rbar == 0) return;
+    const int64_t r = d->r;
+    const int64_t cw = d->c >> 6;
+    if ((int)blockIdx.x >= nbr) {
+        // stripe words of the rows above the block: the update's table index
+        const int64_t stride = (int64_t)(gridDim.x - nbr) * blockDim.x;
+        for (int64_t i = (int64_t)(blockIdx.x - nbr) * blockDim.x + threadIdx.x; i < r; i += stride)
+            IDX[i] = A[i * ld + cw];
+        return;
+    }
+    __shared__ uint64_t sU[KS], sM[KS];
+    __shared__ uint64_t sIn[KS][4];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        // U11 rows over the block's pivot columns, then U11^-1 column by
+        // column (backward substitution U x = e_col), rows by ballot.
+        for (int p = lane; p < rbar; p += 32) {
+            const uint64_t e = d->E11[p];
+            uint64_t u = 0;
+            for (int q = 0; q < rbar; ++q) u |= ((e >> d->qbar[q]) & 1ull) << q;
+            sU[p] = u;
+        }
+        __syncwarp();
+        uint64_t x0 = 0, x1 = 0;
+        for (int p = rbar - 1; p >= 0; --p) {
+            const uint64_t up = sU[p];
+            x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(up & x0)) & 1) << p;
+            x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(up & x1)) & 1) << p;
+        }
+        for (int p = 0; p < rbar; ++p) {
+            const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
+            const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
+            if (lane == 0) sM[p] = ((uint64_t)hi << 32) | lo;
+        }
+    }
+    __syncthreads();
+    // rows <- U11^-1 rows over words [cw, W), four words per step
+    const int p = tid >> 2, wq = tid & 3;
+    for (int64_t wb = cw + (int64_t)blockIdx.x * 4; wb < W; wb += (int64_t)nbr * 4) {
+        const int64_t w = wb + wq;
+        sIn[p][wq] = (p < rbar && w < W) ? A[(r + p) * ld + w] : 0ull;
+        __syncthreads();
+        if (p < rbar && w < W) {
+            const uint64_t mrow = sM[p];
+            uint64_t acc = 0;
+            for (int q = 0; q < rbar; ++q) acc ^= sIn[q][wq] & (0ull - ((mrow >> q) & 1ull));
+            A[(r + p) * ld + w] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
+                             const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms)
+{
+    // block-reduce CTAs: enough to cover the words right of the stripe start
+    // (an upper bound: the stripe start is only known on the device)
+    int64_t nbr = (W + 3) / 4;
+    if (nbr > 2 * num_sms) nbr = 2 * num_sms;
+    if (nbr < 1) nbr = 1;
+    int64_t nidx = (m + RPREP_THREADS - 1) / RPREP_THREADS;
+    if (nidx > 2 * num_sms) nidx = 2 * num_sms;
+    if (nidx < 1) nidx = 1;
+    rref_prep_kernel<<<(int)(nbr + nidx), RPREP_THREADS, 0, st>>>(A, ld, W, s, descs, IDX, (int)nbr);
+    return cudaGetLastError();
+}
+
+__global__ void copy_rank_kernel(const int64_t *r_dev, int64_t *rank_dev) { *rank_dev = *r_dev; }
+
+cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev)
+{
+    copy_rank_kernel<<<1, 1, 0, st>>>(r_dev, rank_dev);
+    return cudaGetLastError();
+}
+
+// ---- solve: consistency of the transformed right-hand side, then X
+
+// flag <- 1 when some row >= rank of the right-hand-side words is nonzero
+__global__ void solve_check_kernel(const uint64_t *Aug, int64_t ldaug, int64_t n, int64_t wa,
+                                   int64_t wb, const int64_t *r_dev, int32_t *flag)
+{
+    const int64_t r = *r_dev;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (n - r) * wb; t += stride) {
+        const int64_t i = r + t / wb, w = t % wb;
+        if (Aug[i * ldaug + wa + w]) atomicExch(flag, 1);
+    }
+}
+
+// B <- 0
+__global__ void solve_zero_kernel(uint64_t *B, int64_t ldb, int64_t n, int64_t wb)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * wb; t += stride)
+        B[(t / wb) * ldb + (t % wb)] = 0;
+}
+
+// X[Q[p]] <- reduced right-hand side of pivot row p
+__global__ void solve_scatter_kernel(const uint64_t *Aug, int64_t ldaug, int64_t wa, int64_t wb,
+                                     const int64_t *r_dev, const int64_t *Q, uint64_t *B, int64_t ldb)
+{
+    const int64_t r = *r_dev;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < r * wb; t += stride) {
+        const int64_t p = t / wb, w = t % wb;
+        B[Q[p] * ldb + w] = Aug[p * ldaug + wa + w];
+    }
+}
+
+cudaError_t launch_solve_check(cudaStream_t st, const uint64_t *Aug, int64_t ldaug, int64_t n,
+                               int64_t wa, int64_t wb, const int64_t *r_dev, int32_t *flag)
+{
+    int64_t blocks = (n * wb + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    solve_check_kernel<<<(int)blocks, 256, 0, st>>>(Aug, ldaug, n, wa, wb, r_dev, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_finish(cudaStream_t st, const uint64_t *Aug, int64_t ldaug, int64_t n,
+                                int64_t wa, int64_t wb, const int64_t *r_dev, const int64_t *Q,
+                                uint64_t *B, int64_t ldb)
+{
+    int64_t blocks = (n * wb + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    solve_zero_kernel<<<(int)blocks, 256, 0, st>>>(B, ldb, n, wb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    solve_scatter_kernel<<<(int)blocks, 256, 0, st>>>(Aug, ldaug, wa, wb, r_dev, Q, B, ldb);
+    return cudaGetLastError();
+}
+
+}  // namespace gf2

@@ -1,0 +1,231 @@
+// kernels_update.cu -- the tabulated trailing update (the hot loop).
+//
+// For every row i of a row range and every word of a column range:
+//     row_i ^= T_0[idx_i byte 0] ^ T_1[idx_i byte 1] ^ ... ^ T_7[idx_i byte 7]
+// where T_t holds all 256 combinations of the eight generator rows
+// 8t .. 8t+7 (Section 3.2: "a table T of all 2^k linear combinations ...
+// for each row of A22 we perform one row addition from the table"; Appendix
+// A, Algorithms 5 and 6; eight tables of k = 8 bits clear 64 columns per
+// pass, as the implementation's multiple Gray-code tables of Section 4 do).
+// The same kernel serves three callers:
+//   UPD_PLE   rows at positions >= r of Algorithm 2, right of the stripe; the
+//             generators are the stripe's raw pivot rows (staged in S) and
+//             the index is w = v L11^-1, so one lookup applies both
+//             A12 <- L11^-1 A12 (pivot rows) and A22 += L21 A12 (the rest).
+//   UPD_RREF  rows above a pivot block during RREF recovery; generators are
+//             the block's reduced rows indexed by pivot column, the index is
+//             the row's raw stripe word.
+//   UPD_MUL   C ^= A[:, 64 kc .. 64 kc + 63] B[64 kc .. 64 kc + 63, :].
+//
+// GB300 mapping.  The kernel is bound by HBM: each 64-bit word of the
+// trailing block is read and written once per stripe.  A persistent grid of
+// one CTA per SM splits the (column tile x row) space evenly; each CTA builds
+// the eight tables for its column tile of TW = 8 words (64 bytes per row) in
+// 128 KiB of shared memory and streams its rows through them.  Tables are
+// built by doubling inside 32-entry Gray-code segments (255 additions per
+// table and word, the count of Algorithm 6).  Two tables share one 128-byte
+// line (table 2a in bytes 0..63, table 2a+1 in bytes 64..127); the two rows
+// served by one 8-lane quarter-warp visit the tables in the orders
+// t and t^1, so every 16-byte lookup phase hits 32 distinct banks whatever
+// the indices are.
+#include "common.cuh"
+
+namespace gf2 {
+
+__device__ __forceinline__ void build_tables(uint64_t *T, const uint64_t *const *gen, int64_t wbase,
+                                             int64_t W)
+{
+    // 512 threads: table tau (8) x segment q of 32 entries (8) x word w (8)
+    const int t = threadIdx.x;
+    const int w = t & 7, q = (t >> 3) & 7, tau = t >> 6;
+    const int64_t word = wbase + w;
+    const bool inr = word < W;
+    uint64_t g[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint64_t *p = gen[8 * tau + b];
+        g[b] = (p != nullptr && inr) ? p[word] : 0ull;
+    }
+    uint64_t val = ((q & 1) ? g[5] : 0ull) ^ ((q & 2) ? g[6] : 0ull) ^ ((q & 4) ? g[7] : 0ull);
+    uint64_t *Tt = T + (tau >> 1) * (256 * TAB_LINE) + (tau & 1) * TW + w;
+    int x = 0;
+    Tt[(32 * q) * TAB_LINE] = val;
+#pragma unroll
+    for (int i = 1; i < 32; ++i) {
+        // Gray code: step i flips bit b = number of trailing zeros of i
+        const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4;
+        x ^= 1 << b;
+        val ^= g[b];
+        Tt[(32 * q + x) * TAB_LINE] = val;
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
+{
+    extern __shared__ __align__(16) uint64_t T[];
+    __shared__ const uint64_t *sGen[KS];
+
+    int64_t row_lo, row_hi, w_lo;
+    const int64_t W = a.W;
+    int64_t r = 0;
+    int maxpos = -1, nS = 0;
+    const StripeDesc *d = a.desc;
+    if (a.mode == UPD_PLE) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        r = d->r;
+        row_lo = r;
+        row_hi = a.m;
+        w_lo = (d->c >> 6) + 1;
+        maxpos = d->maxpos;
+        nS = d->nS;
+        if (threadIdx.x < KS)
+            sGen[threadIdx.x] = (threadIdx.x < rbar) ? a.S + threadIdx.x * a.ldS : nullptr;
+    } else if (a.mode == UPD_RREF) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        row_lo = 0;
+        row_hi = d->r;
+        w_lo = d->c >> 6;
+        if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
+        __syncthreads();
+        if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;
+    } else {
+        row_lo = a.row_lo;
+        row_hi = a.row_hi;
+        w_lo = a.w_lo;
+        if (threadIdx.x < KS)
+            sGen[threadIdx.x] = (threadIdx.x < a.gen_count) ? a.B + threadIdx.x * a.ldb : nullptr;
+    }
+    __syncthreads();
+
+    // PLE: staged rows get their left part (old L bits, new L bits, stripe)
+    if (a.mode == UPD_PLE) {
+        for (int k = blockIdx.x; k < nS; k += gridDim.x) {
+            const uint64_t *src = a.S + (int64_t)k * a.ldS;
+            uint64_t *dst = a.A + (r + d->S_off[k]) * a.ld;
+            for (int64_t w = threadIdx.x; w < w_lo; w += blockDim.x) dst[w] = src[w];
+        }
+    }
+
+    const int64_t R = row_hi - row_lo;
+    if (R <= 0 || w_lo >= W) return;
+    const int64_t a0 = w_lo / TW, a1 = (W + TW - 1) / TW;
+    const int64_t NT = a1 - a0;
+    const int64_t U = NT * R;
+    const int64_t u_beg = U * blockIdx.x / gridDim.x;
+    const int64_t u_end = U * (blockIdx.x + 1) / gridDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.bytes)
+        atomicAdd(a.bytes, (unsigned long long)(R * (W - w_lo) * 16));
+
+    const int rs = threadIdx.x >> 2;        // row slot 0..127
+    const int qd = threadIdx.x & 3;         // quad: words 2qd, 2qd+1 of the tile
+    const int rho = rs & 1;                 // table visiting order t ^ rho
+    constexpr int SLOTS = UPD_THREADS / 4;
+    constexpr int RPT = UPD_ROWS_PER_THREAD;
+
+    int64_t cur_tile = -1;
+    for (int64_t u = u_beg; u < u_end;) {
+        const int64_t tile = u / R;
+        const int64_t rr0 = u - tile * R;
+        const int64_t nrows = min(R - rr0, u_end - u);
+        const int64_t wbase = (a0 + tile) * TW;
+        if (tile != cur_tile) {
+            __syncthreads();
+            build_tables(T, sGen, wbase, W);
+            __syncthreads();
+            cur_tile = tile;
+        }
+        const int64_t w0 = wbase + 2 * qd;
+        const bool lo_in = w0 >= w_lo && w0 < W;
+        const bool hi_in = w0 + 1 >= w_lo && w0 + 1 < W;
+        const uint64_t *Tq = T + 2 * qd;
+        for (int64_t rb = 0; rb < nrows; rb += (int64_t)SLOTS * RPT) {
+            int64_t ri[RPT];
+            uint64_t ix[RPT], x0[RPT], x1[RPT];
+            const uint64_t *src[RPT];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int64_t off = rb + (int64_t)k * SLOTS + rs;
+                ri[k] = (off < nrows) ? row_lo + rr0 + off : -1;
+                src[k] = nullptr;
+                ix[k] = 0;
+                if (ri[k] >= 0) {
+                    const int64_t i = ri[k];
+                    ix[k] = a.idx[i * a.idx_stride];
+                    const uint64_t *sp = a.A + i * a.ld;
+                    if (a.mode == UPD_PLE && i - r <= maxpos) {
+                        const int mv = a.map[i];
+                        if (mv >= 0 && (mv >> 8) == a.stripe) sp = a.S + (int64_t)(mv & 255) * a.ldS;
+                    }
+                    src[k] = sp;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                x0[k] = 0;
+                x1[k] = 0;
+                if (src[k]) {
+                    if (VEC && lo_in && hi_in) {
+                        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src[k] + w0);
+                        x0[k] = v.x;
+                        x1[k] = v.y;
+                    } else {
+                        if (lo_in) x0[k] = src[k][w0];
+                        if (hi_in) x1[k] = src[k][w0 + 1];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+#pragma unroll
+                for (int uu = 0; uu < NTAB; ++uu) {
+                    const int tau = uu ^ rho;
+                    const int e = (int)((ix[k] >> (8 * tau)) & 255ull);
+                    const ulonglong2 tv = *reinterpret_cast<const ulonglong2 *>(
+                        Tq + (tau >> 1) * (256 * TAB_LINE) + e * TAB_LINE + (tau & 1) * TW);
+                    x0[k] ^= tv.x;
+                    x1[k] ^= tv.y;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (ri[k] < 0) continue;
+                uint64_t *dst = a.A + ri[k] * a.ld;
+                if (VEC && lo_in && hi_in) {
+                    *reinterpret_cast<ulonglong2 *>(dst + w0) = make_ulonglong2(x0[k], x1[k]);
+                } else {
+                    if (lo_in) dst[w0] = x0[k];
+                    if (hi_in) dst[w0 + 1] = x1[k];
+                }
+            }
+        }
+        u += nrows;
+    }
+}
+
+cudaError_t setup_update_kernel()
+{
+    const int smem = (int)(TAB_WORDS * sizeof(uint64_t));
+    cudaError_t e = cudaFuncSetAttribute(update_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
+{
+    const size_t smem = TAB_WORDS * sizeof(uint64_t);
+    // The vectorised form needs 16-byte aligned rows: even leading dimensions
+    // and 16-byte aligned bases (staged rows too, for the PLE update).
+    const bool vec = (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
+                     (a.mode != UPD_PLE || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
+    if (vec)
+        update_kernel<true><<<num_sms, UPD_THREADS, smem, st>>>(a);
+    else
+        update_kernel<false><<<num_sms, UPD_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gf2
