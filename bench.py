@@ -300,7 +300,7 @@ def run_ours(args):
         del ps, ws
     # PLE alone at the main size
     ple_ms = None
-    if rank == 0:
+    if rank == 0 and args.side:
         P = torch.empty(n, dtype=torch.int64, device=dev)
         pt = []
         for _ in range(3):
@@ -315,7 +315,7 @@ def run_ours(args):
 
     # ---- end to end through the host-buffer C ABI call (pinned buffers)
     e2e = None
-    if rank == 0 or True:
+    if not args.no_e2e:
         pin = torch.empty((m, W), dtype=torch.int64, pin_memory=True)
         pin_src = torch.from_numpy(A.view(np.int64))
         Qh = torch.empty(n, dtype=torch.int64, pin_memory=True)
@@ -364,6 +364,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--no-side", dest="side", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
