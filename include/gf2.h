@@ -149,6 +149,26 @@ int gf2_ple_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t
 int gf2_rref_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
                   int64_t *Q, int64_t *rank);
 
+/*
+ * PLE with no device memory allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- a process
+ * that hands all device memory to its own allocator at start-up, or code
+ * that must not stall on cudaMalloc / cudaFree -- and it needs no handle
+ * (creating one allocates).
+ *   A, P, Q, rank  as gf2_ple (A, P, Q device pointers; rank a host int64*).
+ *   stream         a cudaStream_t passed as void* (NULL: the default stream).
+ * Limits: m <= 4096 and n <= 4096; larger sizes return GF2_EINVAL and enqueue
+ * nothing.  Scratch: one fixed array of about 0.4 MiB inside the library,
+ * held on every GPU that loads the library until the process exits.  The
+ * first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  Every
+ * call shares the array and re-initialises what must start from a known
+ * state; calls whose work overlaps on the GPU race on it.  Synchronises the
+ * stream before returning.
+ */
+int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_words, int64_t *P, int64_t *Q,
+                    int64_t *rank, void *stream);
+
 /* Counters of the work enqueued since the last reset (host struct). */
 typedef struct gf2_stats {
     int64_t kernel_launches;      /* kernels of this library enqueued          */

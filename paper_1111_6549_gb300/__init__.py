@@ -267,3 +267,21 @@ def default_handle(device: int | None = None) -> Handle:
     if h is None:
         h = _default[dev] = Handle(dev)
     return h
+
+
+def ple_noalloc(A, m: int, n: int, P, Q) -> int:
+    """gf2_ple_noalloc: PLE with all scratch in the library's fixed device
+    array (m, n <= 4096), for callers that cannot allocate device memory.
+    Runs on torch's current stream and returns the rank."""
+    import torch
+    L = load()
+    f = L.gf2_ple_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    ld = _mat(A, m, n) if m > 0 and n > 0 else max(A.stride(0), 1)
+    rank = ctypes.c_int64(0)
+    s = torch.cuda.current_stream().cuda_stream
+    _check(f(_dptr(A), m, n, ld, _dptr(P), _dptr(Q), ctypes.byref(rank), ctypes.c_void_p(s)),
+           "gf2_ple_noalloc")
+    return rank.value
