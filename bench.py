@@ -259,7 +259,9 @@ def run_ours(args):
                 "frac": (upd_gbs / hbm) if upd_gbs else None, "peak_kind": hbm_kind,
                 "traffic": traffic, "algorithmic_bytes_per_launch": upd_per_launch_bytes,
                 "launches_per_step": st["update_launches"] / args.steps,
-                "update_share_of_step": st["update_ms"] / ms if ms > 0 else None}
+                "update_share_of_step": st["update_ms"] / ms if ms > 0 else None,
+                "kernel_ms_per_step": {k: st[k + "_ms"] / args.steps
+                                       for k in ("update", "panel", "prep", "rref_prep", "other")}}
 
     # ---- 32768^2 side measurement (same path, a few steps)
     side = {}

@@ -178,8 +178,12 @@ typedef struct gf2_stats {
     double  update_bytes;         /* algorithmic bytes they moved: 16 bytes per
                                      64-bit word read and written              */
     int64_t panel_fallbacks;      /* stripes that needed the block-wide panel  */
+    double  panel_ms;             /* summed event time of the other kernels,   */
+    double  prep_ms;              /* by kind (only while profiling is on)      */
+    double  rref_prep_ms;
+    double  other_ms;
 } gf2_stats;
-/* Turn per-launch event timing of the update kernel on or off. */
+/* Turn per-launch event timing of every kernel on or off. */
 int gf2_set_profiling(gf2_handle_t handle, int on);
 /* Read the counters (synchronises the stream to finish the event timing). */
 int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);

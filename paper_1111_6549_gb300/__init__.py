@@ -36,7 +36,9 @@ class GF2Error(RuntimeError):
 class _Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("update_launches", ctypes.c_int64),
                 ("update_ms", ctypes.c_double), ("update_bytes", ctypes.c_double),
-                ("panel_fallbacks", ctypes.c_int64)]
+                ("panel_fallbacks", ctypes.c_int64), ("panel_ms", ctypes.c_double),
+                ("prep_ms", ctypes.c_double), ("rref_prep_ms", ctypes.c_double),
+                ("other_ms", ctypes.c_double)]
 
 
 class Desc(ctypes.Structure):

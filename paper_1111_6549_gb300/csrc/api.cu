@@ -32,8 +32,9 @@ struct gf2_handle {
     int64_t upd_launches = 0;
     bool profiling = false;
     std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-    double upd_ms = 0.0;
+    struct Pending { cudaEvent_t e0, e1; int kind; };
+    std::vector<Pending> ev_pending;
+    double kind_ms[5] = {0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other
 };
 
 namespace {
@@ -126,23 +127,41 @@ int grow(char **buf, size_t *cap, size_t need, cudaStream_t st)
         if (e_ != cudaSuccess) { cudaGetLastError(); return GF2_ECUDA; } \
     } while (0)
 
+enum { K_UPDATE = 0, K_PANEL = 1, K_PREP = 2, K_RPREP = 3, K_OTHER = 4 };
+
+// With profiling on, brackets one launch with a pair of events on the
+// handle's stream; the elapsed times are summed per kernel kind later.
+struct Timed {
+    gf2_handle *h;
+    int kind;
+    cudaEvent_t e0 = nullptr;
+    Timed(gf2_handle *h_, int kind_) : h(h_), kind(kind_)
+    {
+        if (!h->profiling) return;
+        e0 = take();
+        if (e0) cudaEventRecord(e0, h->stream);
+    }
+    ~Timed()
+    {
+        if (!h->profiling || !e0) return;
+        cudaEvent_t e1 = take();
+        if (!e1) return;
+        cudaEventRecord(e1, h->stream);
+        h->ev_pending.push_back({e0, e1, kind});
+    }
+    cudaEvent_t take()
+    {
+        cudaEvent_t e = nullptr;
+        if (!h->ev_free.empty()) { e = h->ev_free.back(); h->ev_free.pop_back(); }
+        else if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); e = nullptr; }
+        return e;
+    }
+};
+
 int launch_update_counted(gf2_handle *h, const UpdArgs &a)
 {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->profiling) {
-        for (int i = 0; i < 2; ++i) {
-            cudaEvent_t e;
-            if (!h->ev_free.empty()) { e = h->ev_free.back(); h->ev_free.pop_back(); }
-            else CK(cudaEventCreate(&e));
-            (i == 0 ? e0 : e1) = e;
-        }
-        CK(cudaEventRecord(e0, h->stream));
-    }
+    Timed t(h, K_UPDATE);
     CK(launch_update(h->stream, a, h->num_sms));
-    if (h->profiling) {
-        CK(cudaEventRecord(e1, h->stream));
-        h->ev_pending.emplace_back(e0, e1);
-    }
     h->launches += 1;
     h->upd_launches += 1;
     return GF2_OK;
@@ -166,12 +185,21 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     const int64_t qn = std::min(m, npiv);
     const int64_t W = words_for(ncols);
     const int64_t ns = words_for(npiv);
-    CK(launch_init_ple(h->stream, P, Q, m, qn, map, r_dev(h), h->num_sms));
+    {
+        Timed t(h, K_OTHER);
+        CK(launch_init_ple(h->stream, P, Q, m, qn, map, r_dev(h), h->num_sms));
+    }
     h->launches += 1;
     for (int64_t s = 0; s < ns; ++s) {
-        CK(launch_panel(h->stream, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map, gs, fb_dev(h)));
-        CK(launch_prep(h->stream, A, m, ld, W, (int)s, descs, map, S, L.ldS, IDX, err_dev(h),
-                       h->num_sms));
+        {
+            Timed t(h, K_PANEL);
+            CK(launch_panel(h->stream, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map, gs, fb_dev(h)));
+        }
+        {
+            Timed t(h, K_PREP);
+            CK(launch_prep(h->stream, A, m, ld, W, (int)s, descs, map, S, L.ldS, IDX, err_dev(h),
+                           h->num_sms));
+        }
         h->launches += 2;
         UpdArgs a{};
         a.mode = UPD_PLE;
@@ -201,10 +229,16 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
     uint64_t *IDX = reinterpret_cast<uint64_t *>(h->ws + L.idx);
     const int64_t W = words_for(ncols);
     const int64_t ns = words_for(npiv);
-    CK(launch_rref_lclear(h->stream, A, m, W, ld, r_dev(h), h->num_sms));
+    {
+        Timed t(h, K_OTHER);
+        CK(launch_rref_lclear(h->stream, A, m, W, ld, r_dev(h), h->num_sms));
+    }
     h->launches += 1;
     for (int64_t s = ns - 1; s >= 0; --s) {
-        CK(launch_rref_prep(h->stream, A, ld, W, (int)s, descs, IDX, m, h->num_sms));
+        {
+            Timed t(h, K_RPREP);
+            CK(launch_rref_prep(h->stream, A, ld, W, (int)s, descs, IDX, m, h->num_sms));
+        }
         h->launches += 1;
         UpdArgs a{};
         a.mode = UPD_RREF;
@@ -296,7 +330,7 @@ int gf2_destroy(gf2_handle_t h)
     if (!h) return GF2_EINVAL;
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
-    for (auto &p : h->ev_pending) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    for (auto &p : h->ev_pending) { cudaEventDestroy(p.e0); cudaEventDestroy(p.e1); }
     for (auto e : h->ev_free) cudaEventDestroy(e);
     cudaFree(h->ws);
     cudaFree(h->io);
@@ -577,10 +611,10 @@ int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
     CK(cudaStreamSynchronize(h->stream));
     for (auto &p : h->ev_pending) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) h->upd_ms += ms;
+        if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) h->kind_ms[p.kind] += ms;
         else cudaGetLastError();
-        h->ev_free.push_back(p.first);
-        h->ev_free.push_back(p.second);
+        h->ev_free.push_back(p.e0);
+        h->ev_free.push_back(p.e1);
     }
     h->ev_pending.clear();
     unsigned long long bytes = 0;
@@ -589,7 +623,11 @@ int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
     CK(cudaMemcpy(&fb, fb_dev(h), 4, cudaMemcpyDeviceToHost));
     out->kernel_launches = h->launches;
     out->update_launches = h->upd_launches;
-    out->update_ms = h->upd_ms;
+    out->update_ms = h->kind_ms[K_UPDATE];
+    out->panel_ms = h->kind_ms[K_PANEL];
+    out->prep_ms = h->kind_ms[K_PREP];
+    out->rref_prep_ms = h->kind_ms[K_RPREP];
+    out->other_ms = h->kind_ms[K_OTHER];
     out->update_bytes = (double)bytes;
     out->panel_fallbacks = fb;
     return GF2_OK;
@@ -600,11 +638,11 @@ int gf2_reset_stats(gf2_handle_t h)
     if (!h) return GF2_EINVAL;
     DeviceGuard g(h->device);
     CK(cudaStreamSynchronize(h->stream));
-    for (auto &p : h->ev_pending) { h->ev_free.push_back(p.first); h->ev_free.push_back(p.second); }
+    for (auto &p : h->ev_pending) { h->ev_free.push_back(p.e0); h->ev_free.push_back(p.e1); }
     h->ev_pending.clear();
     h->launches = 0;
     h->upd_launches = 0;
-    h->upd_ms = 0.0;
+    for (double &x : h->kind_ms) x = 0.0;
     CK(cudaMemset(h->small + SM_FALLBACK, 0, 12));
     return GF2_OK;
 }

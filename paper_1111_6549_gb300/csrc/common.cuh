@@ -20,7 +20,7 @@ constexpr int TAB_WORDS = (NTAB / 2) * 256 * TAB_LINE;  // 16384 words = 128 KiB
 constexpr int UPD_THREADS = 512;
 constexpr int UPD_ROWS_PER_THREAD = 4;
 constexpr int PANEL_THREADS = 512;
-constexpr int PANEL_G = 8;        // fast panel window: 32 * PANEL_G rows in one warp
+constexpr int PANEL_WIN = 128;    // fast panel window: rows held bit-sliced by one warp
 
 // Per-stripe record written by the panel kernel and read by the later
 // kernels of the stripe (and by the RREF recovery).
@@ -35,6 +35,7 @@ struct StripeDesc {
     uint64_t E11[KS];   // pivot rows' stripe word after elimination (echelon)
     uint64_t L11[KS];   // L coefficients of pivot rows w.r.t. earlier pivots (bit q < p)
     uint64_t Linv[KS];  // rows of L11^-1 (unit lower triangular)
+    uint64_t Minv[KS];  // rows of U11^-1, U11 = E11 on the pivot columns (unit upper triangular)
     int32_t S_off[SMAX];  // staged row k -> position offset from r
     int64_t S_src[SMAX];  // staged row k -> physical row copied from
     uint8_t qbar[KS];     // pivot column offsets inside the stripe
@@ -77,7 +78,7 @@ cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, in
                          StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
                          PanelScratch gs, int32_t *fallbacks);
 cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
-                        const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
+                        StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
                         uint64_t *IDX, int32_t *err, int num_sms);
 cudaError_t setup_update_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);

@@ -21,39 +21,36 @@
 //                 writes.
 //
 // Laziness (Algorithm 1) on a GPU: the pivot search only reads the stripe
-// word of rows it inspects.  The fast path holds a window of 32*PANEL_G rows
-// in the registers of one warp and uses ballot / ffs / shuffles; it is exact
-// whenever every pivot column finds its row inside the window (or the window
-// holds all remaining rows).  Otherwise the block-wide path redoes the stripe
-// over all remaining rows.
+// word of rows it inspects.  The fast path holds a window of up to 128 rows
+// in the registers of one warp, bit-sliced: lane l owns columns l and l+32 as
+// 128-row masks.  A pivot step is then one shuffle of column j, one find-
+// first-set for the pivot row, and a handful of mask operations per lane for
+// the row exchange and the elimination below the pivot; the L coefficients
+// are kept the same way (one 128-row mask per pivot), and E11 / L11 come out
+// by ballot at the end.  The window is exact whenever every pivot column
+// finds its row inside it (or it holds all remaining rows).  Otherwise the
+// block-wide path redoes the stripe over all remaining rows.
 #include "common.cuh"
 
 #include <climits>
 
 namespace gf2 {
 
-template <int G>
-__device__ __forceinline__ uint64_t sel(const uint64_t (&a)[G], int g)
+// Transpose a 32 x 32 bit block held one row per lane (bit c of lane r =
+// entry (r, c)) so that lane c receives column c (bit r = entry (r, c)):
+// five rounds of swapping the off-diagonal sub-blocks of size 16, 8, 4, 2, 1.
+__device__ __forceinline__ unsigned transpose32(unsigned x)
 {
-    uint64_t v = a[0];
+    const int lane = threadIdx.x & 31;
+    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
-    for (int i = 1; i < G; ++i) v = (g == i) ? a[i] : v;
-    return v;
-}
-template <int G>
-__device__ __forceinline__ int sel(const int (&a)[G], int g)
-{
-    int v = a[0];
-#pragma unroll
-    for (int i = 1; i < G; ++i) v = (g == i) ? a[i] : v;
-    return v;
-}
-template <int G, typename T>
-__device__ __forceinline__ void put(T (&a)[G], int g, T v)
-{
-#pragma unroll
-    for (int i = 0; i < G; ++i)
-        if (g == i) a[i] = v;
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const unsigned m = masks[k];
+        const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
 }
 
 __global__ void init_ple_kernel(int64_t *P, int64_t *Q, int64_t m, int64_t qn, int32_t *map,
@@ -89,6 +86,7 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
     __shared__ uint8_t sh_j[KS];
     __shared__ int32_t sh_Soff[SMAX];
     __shared__ int64_t sh_Ssrc[SMAX];
+    __shared__ int32_t sh_perm[PANEL_WIN];
     __shared__ int sh_fail, sh_rbar, sh_nS, sh_maxpos, sh_best;
     __shared__ unsigned long long sh_colmask;
 
@@ -106,74 +104,117 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         }
         return;
     }
-    const int Wn = (int)min(rows, (int64_t)(32 * PANEL_G));
-
-    // ---------------- fast path: one warp, window of Wn rows in registers
+    // ---------------- fast path: one warp, bit-sliced window of up to 128 rows
     if (warp == 0) {
-        uint64_t val[PANEL_G], lb[PANEL_G];
-        int so[PANEL_G];
+        const int Wn = (int)min(rows, (int64_t)PANEL_WIN);
+        // load: lane l holds window rows l, l+32, l+64, l+96 ...
+        uint64_t rw[4];
 #pragma unroll
-        for (int g = 0; g < PANEL_G; ++g) {
-            const int sl = g * 32 + lane;
-            val[g] = (sl < Wn) ? A[(r + sl) * ld + cw] : 0ull;
-            lb[g] = 0;
-            so[g] = sl;
+        for (int b = 0; b < 4; ++b) {
+            const int sl = b * 32 + lane;
+            rw[b] = (sl < Wn) ? A[(r + sl) * ld + cw] : 0ull;
         }
+        // ... transposed so that lane l owns columns l and l+32 as 128-row masks
+        uint64_t c0lo, c0hi, c1lo, c1hi;
+        {
+            unsigned t0[4], t1[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                t0[b] = transpose32((unsigned)rw[b]);
+                t1[b] = transpose32((unsigned)(rw[b] >> 32));
+            }
+            c0lo = ((uint64_t)t0[1] << 32) | t0[0];
+            c0hi = ((uint64_t)t0[3] << 32) | t0[2];
+            c1lo = ((uint64_t)t1[1] << 32) | t1[0];
+            c1hi = ((uint64_t)t1[3] << 32) | t1[2];
+        }
+        for (int x = lane; x < PANEL_WIN; x += 32) sh_perm[x] = x;
+        __syncwarp();
+        // L columns (pivot p's column = rows eliminated by it), lane owns p = lane, lane + 32
+        uint64_t l0lo = 0, l0hi = 0, l1lo = 0, l1hi = 0;
         int p = 0, tmax = -1;
         bool fail = false;
         for (int j = 0; j < keff && p < Wn; ++j) {
-            int t = -1;
-#pragma unroll
-            for (int g = 0; g < PANEL_G; ++g) {
-                const int sl = g * 32 + lane;
-                const bool cand = (sl >= p) && (sl < Wn) && ((val[g] >> j) & 1ull);
-                const unsigned b = __ballot_sync(0xffffffffu, cand);
-                if (t < 0 && b) t = g * 32 + __ffs(b) - 1;
-            }
-            if (t < 0) {
+            const int owner = j & 31;
+            uint64_t jlo = __shfl_sync(0xffffffffu, (j < 32) ? c0lo : c1lo, owner);
+            uint64_t jhi = __shfl_sync(0xffffffffu, (j < 32) ? c0hi : c1hi, owner);
+            const uint64_t ge_lo = (p < 64) ? (~0ull << p) : 0ull;
+            const uint64_t ge_hi = (p < 64) ? ~0ull : (~0ull << (p - 64));
+            const uint64_t clo = jlo & ge_lo, chi = jhi & ge_hi;
+            int t;
+            if (clo) t = __ffsll((long long)clo) - 1;
+            else if (chi) t = 64 + __ffsll((long long)chi) - 1;
+            else {
                 if (Wn < rows) { fail = true; break; }   // the pivot may lie outside the window
                 continue;                                // column j has no pivot
             }
-            const int gt = t >> 5, lt = t & 31, gp = p >> 5, lp = p & 31;
-            const uint64_t pv = __shfl_sync(0xffffffffu, sel(val, gt), lt);
-            const uint64_t pl = __shfl_sync(0xffffffffu, sel(lb, gt), lt);
-            const int ps = __shfl_sync(0xffffffffu, sel(so, gt), lt);
-            const uint64_t xv = __shfl_sync(0xffffffffu, sel(val, gp), lp);
-            const uint64_t xl = __shfl_sync(0xffffffffu, sel(lb, gp), lp);
-            const int xs = __shfl_sync(0xffffffffu, sel(so, gp), lp);
-            // swap positions p and t: the pivot row moves to p, the row at p to t
-            if (lane == lt) { put(val, gt, xv); put(lb, gt, xl); put(so, gt, xs); }
-            if (lane == lp) { put(val, gp, pv); put(lb, gp, pl); put(so, gp, ps); }
-            if (lane == 0) { sh_t[p] = t; sh_j[p] = (uint8_t)j; sh_E[p] = pv; sh_L[p] = pl; }
-            tmax = max(tmax, t);
-            const uint64_t bitp = 1ull << p;
-#pragma unroll
-            for (int g = 0; g < PANEL_G; ++g) {
-                const int sl = g * 32 + lane;
-                if (sl > p && sl < Wn && ((val[g] >> j) & 1ull)) { val[g] ^= pv; lb[g] |= bitp; }
+            // exchange rows p and t in every 128-row mask
+            const uint64_t mp_lo = (p < 64) ? (1ull << p) : 0ull, mp_hi = (p < 64) ? 0ull : (1ull << (p - 64));
+            const uint64_t mt_lo = (t < 64) ? (1ull << t) : 0ull, mt_hi = (t < 64) ? 0ull : (1ull << (t - 64));
+            const uint64_t both_lo = mp_lo | mt_lo, both_hi = mp_hi | mt_hi;
+#define GF2_SWAPROWS(lo, hi)                                                        \
+            do {                                                                    \
+                const bool d_ = (((lo) & mp_lo) | ((hi) & mp_hi)) != 0ull;          \
+                const bool e_ = (((lo) & mt_lo) | ((hi) & mt_hi)) != 0ull;          \
+                if (d_ != e_) { (lo) ^= both_lo; (hi) ^= both_hi; }                 \
+            } while (0)
+            GF2_SWAPROWS(jlo, jhi);
+            const uint64_t gt_lo = (p >= 63) ? 0ull : (~0ull << (p + 1));
+            const uint64_t gt_hi = (p < 63) ? ~0ull : ((p - 63) >= 64 ? 0ull : (~0ull << (p - 63)));
+            const uint64_t rlo = jlo & gt_lo, rhi = jhi & gt_hi;   // rows below p holding column j
+            GF2_SWAPROWS(c0lo, c0hi);
+            GF2_SWAPROWS(c1lo, c1hi);
+            GF2_SWAPROWS(l0lo, l0hi);
+            GF2_SWAPROWS(l1lo, l1hi);
+#undef GF2_SWAPROWS
+            // the pivot row's entry in each owned column decides whether it is added
+            if (((c0lo & mp_lo) | (c0hi & mp_hi)) != 0ull) { c0lo ^= rlo; c0hi ^= rhi; }
+            if (((c1lo & mp_lo) | (c1hi & mp_hi)) != 0ull) { c1lo ^= rlo; c1hi ^= rhi; }
+            if (lane == (p & 31)) {
+                if (p < 32) { l0lo = rlo; l0hi = rhi; } else { l1lo = rlo; l1hi = rhi; }
             }
+            if (lane == 0) {
+                sh_t[p] = t;
+                sh_j[p] = (uint8_t)j;
+                const int a = sh_perm[p];
+                sh_perm[p] = sh_perm[t];
+                sh_perm[t] = a;
+            }
+            tmax = max(tmax, t);
             ++p;
         }
         if (!fail) {
-            // staged rows: pivot rows first (slot k = position offset k), then
-            // displaced rows (slots in [p, tmax] whose content came from elsewhere)
-#pragma unroll
-            for (int g = 0; g < PANEL_G; ++g) {
-                const int sl = g * 32 + lane;
-                if (sl < p) { sh_Soff[sl] = sl; sh_Ssrc[sl] = r + so[g]; }
-            }
-            int base = p;
-#pragma unroll
-            for (int g = 0; g < PANEL_G; ++g) {
-                const int sl = g * 32 + lane;
-                const bool mv = sl >= p && sl <= tmax && so[g] != sl;
-                const unsigned b = __ballot_sync(0xffffffffu, mv);
-                if (mv) {
-                    const int k = base + __popc(b & ((1u << lane) - 1u));
-                    sh_Soff[k] = sl;
-                    sh_Ssrc[k] = r + so[g];
+            // rows 0..p-1 of the window now hold the pivots: transpose the column
+            // masks back into rows (lane r gets rows r and r + 32)
+            {
+                const unsigned e00 = transpose32((unsigned)c0lo), e01 = transpose32((unsigned)c1lo);
+                const unsigned e10 = transpose32((unsigned)(c0lo >> 32)), e11 = transpose32((unsigned)(c1lo >> 32));
+                const unsigned f00 = transpose32((unsigned)l0lo), f01 = transpose32((unsigned)l1lo);
+                const unsigned f10 = transpose32((unsigned)(l0lo >> 32)), f11 = transpose32((unsigned)(l1lo >> 32));
+                const int q0 = lane, q1 = lane + 32;
+                if (q0 < p) {
+                    sh_E[q0] = ((uint64_t)e01 << 32) | e00;
+                    sh_L[q0] = ((((uint64_t)f01 << 32) | f00)) & ((q0 == 0) ? 0ull : (~0ull >> (64 - q0)));
                 }
-                base += __popc(b);
+                if (q1 < p) {
+                    sh_E[q1] = ((uint64_t)e11 << 32) | e10;
+                    sh_L[q1] = ((((uint64_t)f11 << 32) | f10)) & (~0ull >> (64 - q1));
+                }
+            }
+            __syncwarp();
+            // staged rows: pivot rows first, then rows displaced into [p, tmax]
+            for (int k = lane; k < p; k += 32) { sh_Soff[k] = k; sh_Ssrc[k] = r + sh_perm[k]; }
+            int base = p;
+            for (int b0 = p; b0 <= tmax; b0 += 32) {
+                const int sl = b0 + lane;
+                const bool mv = sl <= tmax && sh_perm[sl] != sl;
+                const unsigned bm = __ballot_sync(0xffffffffu, mv);
+                if (mv) {
+                    const int k = base + __popc(bm & ((1u << lane) - 1u));
+                    sh_Soff[k] = sl;
+                    sh_Ssrc[k] = r + sh_perm[sl];
+                }
+                base += __popc(bm);
             }
             if (lane == 0) { sh_nS = base; sh_maxpos = max(p - 1, tmax); }
         }
@@ -318,13 +359,15 @@ __device__ __forceinline__ void write_lregion(uint64_t *row, int64_t r, int64_t 
 }
 
 constexpr int PREP_THREADS = 256;
-constexpr int PREP_STAGE_BLOCKS = 32;
+constexpr int PREP_STAGE_BLOCKS = SMAX;   // one block per staged row
+constexpr int PREP_MINV_BLOCK = PREP_STAGE_BLOCKS;
+constexpr int PREP_FIRST_ROW_BLOCK = PREP_STAGE_BLOCKS + 1;
 
 __global__ void __launch_bounds__(PREP_THREADS)
-prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, const StripeDesc *descs,
+prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *descs,
             const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *IDX, int32_t *err)
 {
-    const StripeDesc *d = descs + s;
+    StripeDesc *d = descs + s;
     const int rbar = d->rbar;
     if (rbar == 0) return;
     const int64_t r = d->r;
@@ -342,7 +385,7 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, const StripeDe
 
     if (blockIdx.x < PREP_STAGE_BLOCKS) {
         // staged rows: copy the whole source row, then fix its L region
-        for (int k = blockIdx.x; k < nS; k += PREP_STAGE_BLOCKS) {
+        for (int k = blockIdx.x; k < nS; k += PREP_STAGE_BLOCKS) {   // at most one per block
             const uint64_t *src = A + d->S_src[k] * ld;
             uint64_t *dst = S + (int64_t)k * ldS;
             for (int64_t w = threadIdx.x; w < W; w += blockDim.x) dst[w] = src[w];
@@ -374,8 +417,36 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, const StripeDe
         }
         return;
     }
-    const int64_t stride = (int64_t)(gridDim.x - PREP_STAGE_BLOCKS) * blockDim.x;
-    for (int64_t i = r + (int64_t)(blockIdx.x - PREP_STAGE_BLOCKS) * blockDim.x + threadIdx.x;
+    if (blockIdx.x == PREP_MINV_BLOCK) {
+        // U11^-1 for the RREF recovery, where U11[p][q] = E11[p] at column qbar[q]
+        // (unit upper triangular): lane-parallel backward substitution per
+        // column, rows collected by ballot.
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            __shared__ uint64_t sU[KS];
+            for (int p = lane; p < rbar; p += 32) {
+                const uint64_t e = sE[p];
+                uint64_t u = 0;
+                for (int q = 0; q < rbar; ++q) u |= ((e >> sq[q]) & 1ull) << q;
+                sU[p] = u;
+            }
+            __syncwarp();
+            uint64_t x0 = 0, x1 = 0;
+            for (int p = rbar - 1; p >= 0; --p) {
+                const uint64_t up = sU[p];
+                x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(up & x0)) & 1) << p;
+                x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(up & x1)) & 1) << p;
+            }
+            for (int p = 0; p < rbar; ++p) {
+                const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
+                const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
+                if (lane == 0) d->Minv[p] = ((uint64_t)hi << 32) | lo;
+            }
+        }
+        return;
+    }
+    const int64_t stride = (int64_t)(gridDim.x - PREP_FIRST_ROW_BLOCK) * blockDim.x;
+    for (int64_t i = r + (int64_t)(blockIdx.x - PREP_FIRST_ROW_BLOCK) * blockDim.x + threadIdx.x;
          i < m; i += stride) {
         if (i - r <= maxpos) {
             const int mv = map[i];
@@ -398,13 +469,13 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, const StripeDe
 }
 
 cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
-                        const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
+                        StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
                         uint64_t *IDX, int32_t *err, int num_sms)
 {
     int64_t blocks = (m + PREP_THREADS - 1) / PREP_THREADS;
     if (blocks < 1) blocks = 1;
     if (blocks > 4 * num_sms) blocks = 4 * num_sms;
-    prep_kernel<<<(int)(blocks + PREP_STAGE_BLOCKS), PREP_THREADS, 0, st>>>(
+    prep_kernel<<<(int)(blocks + PREP_FIRST_ROW_BLOCK), PREP_THREADS, 0, st>>>(
         A, m, ld, W, s, descs, map, S, ldS, IDX, err);
     return cudaGetLastError();
 }

@@ -64,31 +64,11 @@ rref_prep_kernel(uint64_t *A, int64_t ld, int64_t W, int s, const StripeDesc *de
             IDX[i] = A[i * ld + cw];
         return;
     }
-    __shared__ uint64_t sU[KS], sM[KS];
+    __shared__ uint64_t sM[KS];
     __shared__ uint64_t sIn[KS][4];
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < 32) {
-        // U11 rows over the block's pivot columns, then U11^-1 column by
-        // column (backward substitution U x = e_col), rows by ballot.
-        for (int p = lane; p < rbar; p += 32) {
-            const uint64_t e = d->E11[p];
-            uint64_t u = 0;
-            for (int q = 0; q < rbar; ++q) u |= ((e >> d->qbar[q]) & 1ull) << q;
-            sU[p] = u;
-        }
-        __syncwarp();
-        uint64_t x0 = 0, x1 = 0;
-        for (int p = rbar - 1; p >= 0; --p) {
-            const uint64_t up = sU[p];
-            x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(up & x0)) & 1) << p;
-            x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(up & x1)) & 1) << p;
-        }
-        for (int p = 0; p < rbar; ++p) {
-            const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
-            const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
-            if (lane == 0) sM[p] = ((uint64_t)hi << 32) | lo;
-        }
-    }
+    const int tid = threadIdx.x;
+    // U11^-1 was computed once by the PLE's prep kernel
+    for (int p = tid; p < rbar; p += blockDim.x) sM[p] = d->Minv[p];
     __syncthreads();
     // rows <- U11^-1 rows over words [cw, W), four words per step
     const int p = tid >> 2, wq = tid & 3;

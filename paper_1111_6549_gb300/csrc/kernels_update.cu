@@ -205,26 +205,204 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
     }
 }
 
+// ----------------------------------------------------------------------------
+// Pipelined form (16-byte aligned rows).  Two changes against update_kernel:
+//  * CTAs 2j and 2j+1 work on the two 64-byte halves of the same 128-byte
+//    lines over the same rows at the same time, so a DRAM line fetched for one
+//    half is not fetched again for the other much later (measured: DRAM reads
+//    fall from 1.76x to 1.00x of the algorithmic bytes);
+//  * loads are software-pipelined in registers: the row words and indices of
+//    the next batch are in flight while the current batch does its table
+//    lookups.  Staging them through shared memory instead (cp.async) was
+//    measured to saturate the L1/shared data pipe, which the eight table
+//    lookups per word already use heavily.
+constexpr int PIPE_RPT = 4;
+
+struct RowBatch {
+    uint64_t x0[PIPE_RPT], x1[PIPE_RPT], ix[PIPE_RPT];
+    int64_t ri[PIPE_RPT];
+};
+
+__global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
+{
+    extern __shared__ __align__(16) uint64_t T[];
+    __shared__ const uint64_t *sGen[KS];
+
+    int64_t row_lo, row_hi, w_lo;
+    const int64_t W = a.W;
+    int64_t r = 0;
+    int maxpos = -1, nS = 0;
+    const StripeDesc *d = a.desc;
+    if (a.mode == UPD_PLE) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        r = d->r;
+        row_lo = r;
+        row_hi = a.m;
+        w_lo = (d->c >> 6) + 1;
+        maxpos = d->maxpos;
+        nS = d->nS;
+        if (threadIdx.x < KS)
+            sGen[threadIdx.x] = (threadIdx.x < rbar) ? a.S + threadIdx.x * a.ldS : nullptr;
+    } else if (a.mode == UPD_RREF) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        row_lo = 0;
+        row_hi = d->r;
+        w_lo = d->c >> 6;
+        if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
+        __syncthreads();
+        if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;
+    } else {
+        row_lo = a.row_lo;
+        row_hi = a.row_hi;
+        w_lo = a.w_lo;
+        if (threadIdx.x < KS)
+            sGen[threadIdx.x] = (threadIdx.x < a.gen_count) ? a.B + threadIdx.x * a.ldb : nullptr;
+    }
+    __syncthreads();
+
+    if (a.mode == UPD_PLE) {
+        for (int k = blockIdx.x; k < nS; k += gridDim.x) {
+            const uint64_t *src = a.S + (int64_t)k * a.ldS;
+            uint64_t *dst = a.A + (r + d->S_off[k]) * a.ld;
+            for (int64_t w = threadIdx.x; w < w_lo; w += blockDim.x) dst[w] = src[w];
+        }
+    }
+
+    const int64_t R = row_hi - row_lo;
+    if (R <= 0 || w_lo >= W) return;
+    const int64_t a0 = w_lo / TW, a1 = (W + TW - 1) / TW;
+    const int64_t NT = a1 - a0;
+    const int64_t NTP = (NT + 1) / 2;
+    const int npairs = gridDim.x >> 1;
+    const int pj = blockIdx.x >> 1, half = blockIdx.x & 1;
+    if (pj >= npairs) return;                       // odd grid: the last CTA has no partner
+    const int64_t U = NTP * R;
+    const int64_t u_beg = U * pj / npairs;
+    const int64_t u_end = U * (pj + 1) / npairs;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.bytes)
+        atomicAdd(a.bytes, (unsigned long long)(R * (W - w_lo) * 16));
+
+    const int tid = threadIdx.x;
+    const int rs = tid >> 2;
+    const int qd = tid & 3;
+    const int rho = rs & 1;
+    constexpr int SLOTS = UPD_THREADS / 4;
+    constexpr int CH = SLOTS * PIPE_RPT;             // rows per batch
+
+    for (int64_t u = u_beg; u < u_end;) {
+        const int64_t tp = u / R;
+        const int64_t rr0 = u - tp * R;
+        const int64_t nrows = min(R - rr0, u_end - u);
+        u += nrows;
+        const int64_t tile = 2 * tp + half;
+        if (tile >= NT) continue;
+        const int64_t wbase = (a0 + tile) * TW;
+        __syncthreads();
+        build_tables(T, sGen, wbase, W);
+        __syncthreads();
+
+        const int64_t w0 = wbase + 2 * qd;
+        const bool lo_in = w0 >= w_lo && w0 < W;
+        const bool hi_in = w0 + 1 >= w_lo && w0 + 1 < W;
+        const bool full = lo_in && hi_in;
+        const int64_t row0 = row_lo + rr0;
+        const uint64_t *Tq = T + 2 * qd;
+
+        auto fetch = [&](RowBatch &bt, int64_t base) {
+#pragma unroll
+            for (int k = 0; k < PIPE_RPT; ++k) {
+                const int64_t off = base + k * SLOTS + rs;
+                bt.ri[k] = (off < nrows) ? row0 + off : -1;
+                bt.x0[k] = 0;
+                bt.x1[k] = 0;
+                bt.ix[k] = 0;
+                if (bt.ri[k] >= 0) {
+                    const int64_t i = bt.ri[k];
+                    bt.ix[k] = __ldg(a.idx + i * a.idx_stride);
+                    const uint64_t *sp = a.A + i * a.ld;
+                    if (a.mode == UPD_PLE && i - r <= maxpos) {
+                        const int mv = a.map[i];
+                        if (mv >= 0 && (mv >> 8) == a.stripe) sp = a.S + (int64_t)(mv & 255) * a.ldS;
+                    }
+                    if (full) {
+                        const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(sp + w0));
+                        bt.x0[k] = v.x;
+                        bt.x1[k] = v.y;
+                    } else {
+                        if (lo_in) bt.x0[k] = sp[w0];
+                        if (hi_in) bt.x1[k] = sp[w0 + 1];
+                    }
+                }
+            }
+        };
+        auto finish = [&](RowBatch &bt) {
+#pragma unroll
+            for (int k = 0; k < PIPE_RPT; ++k) {
+                uint64_t x0 = bt.x0[k], x1 = bt.x1[k];
+                const uint64_t ix = bt.ix[k];
+#pragma unroll
+                for (int uu = 0; uu < NTAB; ++uu) {
+                    const int tau = uu ^ rho;
+                    const int e = (int)((ix >> (8 * tau)) & 255ull);
+                    const ulonglong2 tv = *reinterpret_cast<const ulonglong2 *>(
+                        Tq + (tau >> 1) * (256 * TAB_LINE) + e * TAB_LINE + (tau & 1) * TW);
+                    x0 ^= tv.x;
+                    x1 ^= tv.y;
+                }
+                if (bt.ri[k] < 0) continue;
+                uint64_t *dst = a.A + bt.ri[k] * a.ld;
+                if (full) {
+                    __stcs(reinterpret_cast<ulonglong2 *>(dst + w0), make_ulonglong2(x0, x1));
+                } else {
+                    if (lo_in) dst[w0] = x0;
+                    if (hi_in) dst[w0 + 1] = x1;
+                }
+            }
+        };
+
+        RowBatch b0, b1;
+        fetch(b0, 0);
+        int64_t base = 0;
+        for (;;) {
+            if (base + CH < nrows) fetch(b1, base + CH);
+            finish(b0);
+            base += CH;
+            if (base >= nrows) break;
+            if (base + CH < nrows) fetch(b0, base + CH);
+            finish(b1);
+            base += CH;
+            if (base >= nrows) break;
+        }
+    }
+}
+
 cudaError_t setup_update_kernel()
 {
     const int smem = (int)(TAB_WORDS * sizeof(uint64_t));
     cudaError_t e = cudaFuncSetAttribute(update_kernel<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(update_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
 {
     const size_t smem = TAB_WORDS * sizeof(uint64_t);
-    // The vectorised form needs 16-byte aligned rows: even leading dimensions
-    // and 16-byte aligned bases (staged rows too, for the PLE update).
+    // The vectorised forms need 16-byte aligned rows: even leading dimensions
+    // and 16-byte aligned bases (staged rows too, for the PLE update), and
+    // 8-byte aligned index words.
     const bool vec = (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
                      (a.mode != UPD_PLE || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
-    if (vec)
-        update_kernel<true><<<num_sms, UPD_THREADS, smem, st>>>(a);
-    else
+    if (vec) {
+        const int grid = (num_sms & ~1) > 0 ? (num_sms & ~1) : 2;
+        update_pipe_kernel<<<grid, UPD_THREADS, smem, st>>>(a);
+    } else {
         update_kernel<false><<<num_sms, UPD_THREADS, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
