@@ -183,7 +183,7 @@ typedef struct gf2_stats {
     double  rref_prep_ms;
     double  other_ms;
 } gf2_stats;
-/* Turn per-launch event timing of every kernel on or off. */
+/* Per-launch event timing: 0 off, 1 the update kernel only, 2 every kernel. */
 int gf2_set_profiling(gf2_handle_t handle, int on);
 /* Read the counters (synchronises the stream to finish the event timing). */
 int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);

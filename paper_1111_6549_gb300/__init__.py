@@ -247,8 +247,9 @@ class Handle:
         return rank.value
 
     # ---- statistics -----------------------------------------------------
-    def set_profiling(self, on: bool) -> None:
-        _check(load().gf2_set_profiling(self._h, 1 if on else 0), "gf2_set_profiling")
+    def set_profiling(self, level) -> None:
+        """0: off, 1 (or True): time the update kernel, 2: time every kernel."""
+        _check(load().gf2_set_profiling(self._h, int(level)), "gf2_set_profiling")
 
     def stats(self) -> dict:
         s = _Stats()

@@ -22,6 +22,9 @@ using namespace gf2;
 struct gf2_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;   // look-ahead panels run here, overlapping the update
+    cudaEvent_t ev_fork = nullptr, ev_u1 = nullptr, ev_p = nullptr;
+    bool lookahead = true;
     int num_sms = 1;
     char *ws = nullptr;        // stripe records, indices, staged rows, panel scratch
     size_t ws_cap = 0;
@@ -30,7 +33,7 @@ struct gf2_handle {
     char *small = nullptr;     // rank, flags, counters
     int64_t launches = 0;
     int64_t upd_launches = 0;
-    bool profiling = false;
+    int profiling = 0;             // 1: time update launches, 2: time every launch
     std::vector<cudaEvent_t> ev_free;
     struct Pending { cudaEvent_t e0, e1; int kind; };
     std::vector<Pending> ev_pending;
@@ -74,7 +77,7 @@ Layout layout_for(int64_t m, int64_t ncols)
     size_t off = 0;
     L.descs = off; off = align256(off + (size_t)ns * sizeof(StripeDesc));
     L.idx = off;   off = align256(off + (size_t)mm * 8);
-    L.map = off;   off = align256(off + (size_t)mm * 4);
+    L.map = off;   off = align256(off + (size_t)mm * 8);   // two halves, by stripe parity
     L.S = off;     off = align256(off + (size_t)SMAX * L.ldS * 8);
     L.gval = off;  off = align256(off + (size_t)mm * 8);
     L.glb = off;   off = align256(off + (size_t)mm * 8);
@@ -134,19 +137,21 @@ enum { K_UPDATE = 0, K_PANEL = 1, K_PREP = 2, K_RPREP = 3, K_OTHER = 4 };
 struct Timed {
     gf2_handle *h;
     int kind;
+    cudaStream_t st;
     cudaEvent_t e0 = nullptr;
-    Timed(gf2_handle *h_, int kind_) : h(h_), kind(kind_)
+    Timed(gf2_handle *h_, int kind_, cudaStream_t st_ = nullptr)
+        : h(h_), kind(kind_), st(st_ ? st_ : h_->stream)
     {
-        if (!h->profiling) return;
+        if (h->profiling == 0 || (h->profiling == 1 && kind != K_UPDATE)) return;
         e0 = take();
-        if (e0) cudaEventRecord(e0, h->stream);
+        if (e0) cudaEventRecord(e0, st);
     }
     ~Timed()
     {
-        if (!h->profiling || !e0) return;
+        if (!e0) return;
         cudaEvent_t e1 = take();
         if (!e1) return;
-        cudaEventRecord(e1, h->stream);
+        cudaEventRecord(e1, st);
         h->ev_pending.push_back({e0, e1, kind});
     }
     cudaEvent_t take()
@@ -185,22 +190,30 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     const int64_t qn = std::min(m, npiv);
     const int64_t W = words_for(ncols);
     const int64_t ns = words_for(npiv);
+    // The row map has two halves: stripe s uses half s & 1, so the next
+    // stripe's panel (running early, on the side stream) never overwrites an
+    // entry the current update still reads.
+    auto map_of = [&](int64_t s) { return map + (s & 1) * std::max<int64_t>(m, 1); };
+    CK(cudaMemsetAsync(map, 0xFF, (size_t)std::max<int64_t>(m, 1) * 8, h->stream));
     {
         Timed t(h, K_OTHER);
-        CK(launch_init_ple(h->stream, P, Q, m, qn, map, r_dev(h), h->num_sms));
+        CK(launch_init_ple(h->stream, P, Q, m, qn, nullptr, r_dev(h), h->num_sms));
     }
     h->launches += 1;
-    for (int64_t s = 0; s < ns; ++s) {
-        {
-            Timed t(h, K_PANEL);
-            CK(launch_panel(h->stream, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map, gs, fb_dev(h)));
-        }
-        {
-            Timed t(h, K_PREP);
-            CK(launch_prep(h->stream, A, m, ld, W, (int)s, descs, map, S, L.ldS, IDX, err_dev(h),
-                           h->num_sms));
-        }
-        h->launches += 2;
+    auto panel = [&](cudaStream_t st, int64_t s) -> int {
+        Timed t(h, K_PANEL, st);
+        CK(launch_panel(st, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map_of(s), gs, fb_dev(h)));
+        h->launches += 1;
+        return GF2_OK;
+    };
+    auto prep = [&](int64_t s) -> int {
+        Timed t(h, K_PREP);
+        CK(launch_prep(h->stream, A, m, ld, W, (int)s, descs, map_of(s), S, L.ldS, IDX, err_dev(h),
+                       h->num_sms));
+        h->launches += 1;
+        return GF2_OK;
+    };
+    auto upd = [&](int64_t s, int64_t tp_lo, int64_t tp_hi, int left, int grid) -> int {
         UpdArgs a{};
         a.mode = UPD_PLE;
         a.A = A;
@@ -211,12 +224,52 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
         a.stripe = (int)s;
         a.S = S;
         a.ldS = L.ldS;
-        a.map = map;
+        a.map = map_of(s);
         a.idx = IDX;
         a.idx_stride = 1;
         a.bytes = bytes_dev(h);
-        rc = launch_update_counted(h, a);
-        if (rc) return rc;
+        a.tp_lo = tp_lo;
+        a.tp_hi = tp_hi;
+        a.left_copies = left;
+        a.grid = grid;
+        return launch_update_counted(h, a);
+    };
+    UpdArgs probe{};
+    probe.mode = UPD_PLE;
+    probe.A = A;
+    probe.ld = ld;
+    probe.S = S;
+    probe.ldS = L.ldS;
+    const bool la = h->lookahead && h->side && ns > 1 && update_vectorised(probe) && h->num_sms >= 8;
+    if (!la) {
+        for (int64_t s = 0; s < ns; ++s) {
+            if ((rc = panel(h->stream, s))) return rc;
+            if ((rc = prep(s))) return rc;
+            if ((rc = upd(s, 0, -1, 1, 0))) return rc;
+        }
+        return GF2_OK;
+    }
+    // Look-ahead: U1(s) updates the first tile pair (which holds stripe s+1)
+    // and the staged rows' left parts; the panel of stripe s+1 then runs on
+    // the side stream while U2(s) updates the remaining tile pairs on all
+    // but two SMs; prep(s+1) waits for both.
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    if ((rc = panel(h->stream, 0))) return rc;
+    if ((rc = prep(0))) return rc;
+    for (int64_t s = 0; s < ns; ++s) {
+        if (s + 1 < ns) {
+            if ((rc = upd(s, 0, 1, 1, 0))) return rc;
+            CK(cudaEventRecord(h->ev_u1, h->stream));
+            CK(cudaStreamWaitEvent(h->side, h->ev_u1, 0));
+            if ((rc = panel(h->side, s + 1))) return rc;
+            CK(cudaEventRecord(h->ev_p, h->side));
+            if ((rc = upd(s, 1, -1, 0, h->num_sms - 2))) return rc;
+            CK(cudaStreamWaitEvent(h->stream, h->ev_p, 0));
+            if ((rc = prep(s + 1))) return rc;
+        } else {
+            if ((rc = upd(s, 0, -1, 1, 0))) return rc;
+        }
     }
     return GF2_OK;
 }
@@ -241,6 +294,9 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         }
         h->launches += 1;
         UpdArgs a{};
+        a.tp_lo = 0;
+        a.tp_hi = -1;
+        a.left_copies = 1;
         a.mode = UPD_RREF;
         a.A = A;
         a.ld = ld;
@@ -321,6 +377,13 @@ int gf2_create(gf2_handle_t *handle, int device)
         return GF2_ENOMEM;
     }
     cudaMemset(h->small, 0, SM_BYTES_TOTAL);
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_u1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_p, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        h->lookahead = false;     // the sequential stripe loop needs none of them
+    }
     *handle = h;
     return GF2_OK;
 }
@@ -332,6 +395,10 @@ int gf2_destroy(gf2_handle_t h)
     cudaStreamSynchronize(h->stream);
     for (auto &p : h->ev_pending) { cudaEventDestroy(p.e0); cudaEventDestroy(p.e1); }
     for (auto e : h->ev_free) cudaEventDestroy(e);
+    if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_u1) cudaEventDestroy(h->ev_u1);
+    if (h->ev_p) cudaEventDestroy(h->ev_p);
     cudaFree(h->ws);
     cudaFree(h->io);
     cudaFree(h->small);
@@ -450,6 +517,9 @@ int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t
         CK(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)Wc * 8, (size_t)m, h->stream));
     for (int64_t kc = 0; kc < words_for(k); ++kc) {
         UpdArgs a{};
+        a.tp_lo = 0;
+        a.tp_hi = -1;
+        a.left_copies = 1;
         a.mode = UPD_MUL;
         a.A = C;
         a.ld = ldc;
@@ -600,7 +670,7 @@ int gf2_rref_host(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld,
 int gf2_set_profiling(gf2_handle_t h, int on)
 {
     if (!h) return GF2_EINVAL;
-    h->profiling = on != 0;
+    h->profiling = on < 0 ? 0 : (on > 2 ? 2 : on);
     return GF2_OK;
 }
 

@@ -69,6 +69,9 @@ struct UpdArgs {
     int64_t row_lo, row_hi;    // MUL: rows to update
     int64_t w_lo;              // MUL: first word to update
     unsigned long long *bytes; // algorithmic bytes counter (may be null)
+    int64_t tp_lo, tp_hi;      // tile pairs [tp_lo, tp_hi) of the column range (tp_hi < 0: all)
+    int left_copies;           // PLE: also write the staged rows' left parts
+    int grid;                  // CTAs to launch (0: one per SM)
 };
 
 // ---- launchers (host side, defined in the .cu files) ----
@@ -82,6 +85,7 @@ cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int
                         uint64_t *IDX, int32_t *err, int num_sms);
 cudaError_t setup_update_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
+bool update_vectorised(const UpdArgs &a);   // true when the paired, pipelined form runs
 cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t W, int64_t ld,
                                const int64_t *r_dev, int num_sms);
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,

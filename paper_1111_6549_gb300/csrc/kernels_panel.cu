@@ -293,6 +293,30 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
 
     // ---------------- outputs
     const int rbar = sh_rbar;
+    if (warp == 1) {
+        // U11^-1 for the RREF recovery, U11[p][q] = E11[p] at column qbar[q]
+        // (unit upper triangular): lane-parallel backward substitution per
+        // column, rows collected by ballot.  Runs beside warp 0's L11^-1.
+        __shared__ uint64_t sU[KS];
+        for (int p = lane; p < rbar; p += 32) {
+            const uint64_t e = sh_E[p];
+            uint64_t u = 0;
+            for (int q = 0; q < rbar; ++q) u |= ((e >> sh_j[q]) & 1ull) << q;
+            sU[p] = u;
+        }
+        __syncwarp();
+        uint64_t x0 = 0, x1 = 0;
+        for (int p = rbar - 1; p >= 0; --p) {
+            const uint64_t up = sU[p];
+            x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(up & x0)) & 1) << p;
+            x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(up & x1)) & 1) << p;
+        }
+        for (int p = 0; p < rbar; ++p) {
+            const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
+            const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
+            if (lane == 0) d->Minv[p] = ((uint64_t)hi << 32) | lo;
+        }
+    }
     if (warp == 0) {
         // L11^-1 column by column (lane owns columns lane and lane + 32):
         // forward substitution L x = e_col, then rows by ballot.
@@ -360,8 +384,7 @@ __device__ __forceinline__ void write_lregion(uint64_t *row, int64_t r, int64_t 
 
 constexpr int PREP_THREADS = 256;
 constexpr int PREP_STAGE_BLOCKS = SMAX;   // one block per staged row
-constexpr int PREP_MINV_BLOCK = PREP_STAGE_BLOCKS;
-constexpr int PREP_FIRST_ROW_BLOCK = PREP_STAGE_BLOCKS + 1;
+constexpr int PREP_FIRST_ROW_BLOCK = PREP_STAGE_BLOCKS;
 
 __global__ void __launch_bounds__(PREP_THREADS)
 prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *descs,
@@ -414,34 +437,6 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
                 IDX[pos] = ix;
             }
             __syncthreads();
-        }
-        return;
-    }
-    if (blockIdx.x == PREP_MINV_BLOCK) {
-        // U11^-1 for the RREF recovery, where U11[p][q] = E11[p] at column qbar[q]
-        // (unit upper triangular): lane-parallel backward substitution per
-        // column, rows collected by ballot.
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            __shared__ uint64_t sU[KS];
-            for (int p = lane; p < rbar; p += 32) {
-                const uint64_t e = sE[p];
-                uint64_t u = 0;
-                for (int q = 0; q < rbar; ++q) u |= ((e >> sq[q]) & 1ull) << q;
-                sU[p] = u;
-            }
-            __syncwarp();
-            uint64_t x0 = 0, x1 = 0;
-            for (int p = rbar - 1; p >= 0; --p) {
-                const uint64_t up = sU[p];
-                x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(up & x0)) & 1) << p;
-                x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(up & x1)) & 1) << p;
-            }
-            for (int p = 0; p < rbar; ++p) {
-                const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
-                const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
-                if (lane == 0) d->Minv[p] = ((uint64_t)hi << 32) | lo;
-            }
         }
         return;
     }

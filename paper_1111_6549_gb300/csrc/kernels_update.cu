@@ -215,7 +215,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
 //    the next batch are in flight while the current batch does its table
 //    lookups.  Staging them through shared memory instead (cp.async) was
 //    measured to saturate the L1/shared data pipe, which the eight table
-//    lookups per word already use heavily.
+//    lookups per word already use heavily.  Loads and stores use the default
+//    cache policy: evict-first hints let L2 drop the partner half of a line
+//    before the paired CTA reads it (measured: reads back up to 1.68x).
 constexpr int PIPE_RPT = 4;
 
 struct RowBatch {
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     }
     __syncthreads();
 
-    if (a.mode == UPD_PLE) {
+    if (a.mode == UPD_PLE && a.left_copies) {
         for (int k = blockIdx.x; k < nS; k += gridDim.x) {
             const uint64_t *src = a.S + (int64_t)k * a.ldS;
             uint64_t *dst = a.A + (r + d->S_off[k]) * a.ld;
@@ -275,14 +277,20 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     const int64_t a0 = w_lo / TW, a1 = (W + TW - 1) / TW;
     const int64_t NT = a1 - a0;
     const int64_t NTP = (NT + 1) / 2;
+    const int64_t tp_lo = min(a.tp_lo, NTP);
+    const int64_t tp_hi = (a.tp_hi < 0) ? NTP : min(a.tp_hi, NTP);
+    if (tp_lo >= tp_hi) return;
     const int npairs = gridDim.x >> 1;
     const int pj = blockIdx.x >> 1, half = blockIdx.x & 1;
     if (pj >= npairs) return;                       // odd grid: the last CTA has no partner
-    const int64_t U = NTP * R;
+    const int64_t U = (tp_hi - tp_lo) * R;
     const int64_t u_beg = U * pj / npairs;
     const int64_t u_end = U * (pj + 1) / npairs;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.bytes)
-        atomicAdd(a.bytes, (unsigned long long)(R * (W - w_lo) * 16));
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.bytes) {
+        const int64_t wl = max(w_lo, (a0 + 2 * tp_lo) * TW);
+        const int64_t wh = min(W, (a0 + 2 * tp_hi) * TW);
+        atomicAdd(a.bytes, (unsigned long long)(R * (wh - wl) * 16));
+    }
 
     const int tid = threadIdx.x;
     const int rs = tid >> 2;
@@ -292,11 +300,11 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     constexpr int CH = SLOTS * PIPE_RPT;             // rows per batch
 
     for (int64_t u = u_beg; u < u_end;) {
-        const int64_t tp = u / R;
-        const int64_t rr0 = u - tp * R;
+        const int64_t tq = u / R;
+        const int64_t rr0 = u - tq * R;
         const int64_t nrows = min(R - rr0, u_end - u);
         u += nrows;
-        const int64_t tile = 2 * tp + half;
+        const int64_t tile = 2 * (tp_lo + tq) + half;
         if (tile >= NT) continue;
         const int64_t wbase = (a0 + tile) * TW;
         __syncthreads();
@@ -327,7 +335,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
                         if (mv >= 0 && (mv >> 8) == a.stripe) sp = a.S + (int64_t)(mv & 255) * a.ldS;
                     }
                     if (full) {
-                        const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(sp + w0));
+                        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(sp + w0);
                         bt.x0[k] = v.x;
                         bt.x1[k] = v.y;
                     } else {
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
                 if (bt.ri[k] < 0) continue;
                 uint64_t *dst = a.A + bt.ri[k] * a.ld;
                 if (full) {
-                    __stcs(reinterpret_cast<ulonglong2 *>(dst + w0), make_ulonglong2(x0, x1));
+                    *reinterpret_cast<ulonglong2 *>(dst + w0) = make_ulonglong2(x0, x1);
                 } else {
                     if (lo_in) dst[w0] = x0;
                     if (hi_in) dst[w0 + 1] = x1;
@@ -389,6 +397,12 @@ cudaError_t setup_update_kernel()
     return cudaFuncSetAttribute(update_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
+bool update_vectorised(const UpdArgs &a)
+{
+    return (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
+           (a.mode != UPD_PLE || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
+}
+
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
 {
     const size_t smem = TAB_WORDS * sizeof(uint64_t);
@@ -397,11 +411,13 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
     // 8-byte aligned index words.
     const bool vec = (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
                      (a.mode != UPD_PLE || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
+    int grid = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
     if (vec) {
-        const int grid = (num_sms & ~1) > 0 ? (num_sms & ~1) : 2;
+        grid &= ~1;
+        if (grid < 2) grid = 2;
         update_pipe_kernel<<<grid, UPD_THREADS, smem, st>>>(a);
     } else {
-        update_kernel<false><<<num_sms, UPD_THREADS, smem, st>>>(a);
+        update_kernel<false><<<grid, UPD_THREADS, smem, st>>>(a);
     }
     return cudaGetLastError();
 }

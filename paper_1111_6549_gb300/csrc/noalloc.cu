@@ -135,6 +135,9 @@ extern "C" int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_wor
         NA_CK(launch_panel(st, A, m, ld_words, n, (int)s, descs, r_dev, P, Q, map, gs, fallbacks));
         NA_CK(launch_prep(st, A, m, ld_words, W, (int)s, descs, map, S, NA_LDS, IDX, err, nd->num_sms));
         UpdArgs a{};
+        a.tp_lo = 0;
+        a.tp_hi = -1;
+        a.left_copies = 1;
         a.mode = UPD_PLE;
         a.A = A;
         a.ld = ld_words;
