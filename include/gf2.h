@@ -121,9 +121,12 @@ int gf2_solve(gf2_handle_t handle, uint64_t *A, int64_t n, int64_t lda, uint64_t
               int64_t nrhs, int64_t ldb, int *solve_status);
 
 /*
- * Many independent PLE decompositions in one persistent launch (each as
- * gf2_ple).  descs is a HOST array of count descriptors; A, P, Q and rank in
- * each descriptor are DEVICE pointers (rank: one int64).  Matrices must not
+ * Many independent PLE decompositions (each exactly as gf2_ple).  Matrices
+ * of at most 4096 x 4096 run in one persistent launch in which every CTA
+ * decomposes whole matrices, claimed largest first from a work counter;
+ * larger matrices then run the single-matrix path one after another.
+ * descs is a HOST array of count descriptors; A, P, Q and rank in each
+ * descriptor are DEVICE pointers (rank: one int64).  Matrices must not
  * overlap.  Asynchronous.
  */
 typedef struct gf2_desc {

@@ -30,6 +30,8 @@ struct gf2_handle {
     size_t ws_cap = 0;
     char *io = nullptr;        // host-API device copies, solve's augmented matrix
     size_t io_cap = 0;
+    char *bws = nullptr;       // batched kernel: descriptors, order, per-CTA scratch
+    size_t bws_cap = 0;
     char *small = nullptr;     // rank, flags, counters
     int64_t launches = 0;
     int64_t upd_launches = 0;
@@ -401,6 +403,7 @@ int gf2_destroy(gf2_handle_t h)
     if (h->ev_p) cudaEventDestroy(h->ev_p);
     cudaFree(h->ws);
     cudaFree(h->io);
+    cudaFree(h->bws);
     cudaFree(h->small);
     delete h;
     return GF2_OK;
@@ -593,9 +596,12 @@ int gf2_solve(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, 
     return GF2_OK;
 }
 
+static_assert(sizeof(gf2_desc) == sizeof(gf2_batch_item), "gf2_desc and gf2_batch_item must match");
+
 int gf2_ple_batched(gf2_handle_t h, const gf2_desc *descs, int64_t count)
 {
     if (!h || count < 0 || (count > 0 && !descs)) return GF2_EINVAL;
+    if (count > INT32_MAX / 2) return GF2_EINVAL;
     for (int64_t b = 0; b < count; ++b) {
         const gf2_desc &d = descs[b];
         int rc = check_args(h, d.A, d.m, d.n, d.ld_words);
@@ -603,7 +609,45 @@ int gf2_ple_batched(gf2_handle_t h, const gf2_desc *descs, int64_t count)
         if (!d.rank || (d.m > 0 && !d.P) || (d.m > 0 && d.n > 0 && !d.Q)) return GF2_EINVAL;
     }
     DeviceGuard g(h->device);
+    // Matrices up to BATCH_MAX_ROWS x BATCH_MAX_COLS go to the persistent
+    // batched kernel, largest first; bigger ones take the single-matrix path.
+    std::vector<int32_t> small;
+    std::vector<int64_t> large;
+    int64_t max_rows = 1, max_w = 1;
     for (int64_t b = 0; b < count; ++b) {
+        const gf2_desc &d = descs[b];
+        if (d.m <= BATCH_MAX_ROWS && d.n <= BATCH_MAX_COLS) {
+            small.push_back((int32_t)b);
+            max_rows = std::max(max_rows, d.m);
+            max_w = std::max(max_w, words_for(d.n));
+        } else {
+            large.push_back(b);
+        }
+    }
+    if (!small.empty()) {
+        std::stable_sort(small.begin(), small.end(), [&](int32_t x, int32_t y) {
+            return descs[x].m * descs[x].n > descs[y].m * descs[y].n;
+        });
+        const int64_t ldS = max_w + (max_w & 1);
+        const int grid = (int)std::min<int64_t>(batched_grid(h->num_sms), (int64_t)small.size());
+        const size_t items_bytes = align256((size_t)count * sizeof(gf2_desc));
+        const size_t order_bytes = align256(small.size() * sizeof(int32_t));
+        const size_t next_bytes = 256;
+        const size_t scratch_bytes = align256(batched_scratch_words(max_rows, ldS, grid) * 8);
+        int rc = grow(&h->bws, &h->bws_cap, items_bytes + order_bytes + next_bytes + scratch_bytes, h->stream);
+        if (rc) return rc;
+        auto *items = reinterpret_cast<gf2_batch_item *>(h->bws);
+        auto *order = reinterpret_cast<int32_t *>(h->bws + items_bytes);
+        auto *next = reinterpret_cast<int32_t *>(h->bws + items_bytes + order_bytes);
+        auto *scratch = reinterpret_cast<uint64_t *>(h->bws + items_bytes + order_bytes + next_bytes);
+        CK(cudaMemcpyAsync(items, descs, (size_t)count * sizeof(gf2_desc), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(order, small.data(), small.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           h->stream));
+        CK(cudaMemsetAsync(next, 0, sizeof(int32_t), h->stream));
+        CK(launch_batched(h->stream, items, order, (int)small.size(), next, scratch, max_rows, ldS, grid));
+        h->launches += 1;
+    }
+    for (int64_t b : large) {
         const gf2_desc &d = descs[b];
         int rc = gf2_ple_async(h, d.A, d.m, d.n, d.ld_words, d.P, d.Q, d.rank);
         if (rc) return rc;

@@ -41,6 +41,17 @@ struct StripeDesc {
     uint8_t qbar[KS];     // pivot column offsets inside the stripe
 };
 
+// One matrix of the batched entry point (same layout as gf2_desc).
+struct gf2_batch_item {
+    uint64_t *A;
+    int64_t m, n, ld_words;
+    int64_t *P;
+    int64_t *Q;
+    int64_t *rank;
+};
+constexpr int64_t BATCH_MAX_ROWS = 4096;   // larger matrices take the single-matrix path
+constexpr int64_t BATCH_MAX_COLS = 4096;
+
 // Scratch of the block-wide panel path: one entry per remaining row.
 struct PanelScratch {
     uint64_t *val;   // stripe word, eliminated eagerly
@@ -91,6 +102,11 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
+cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const int32_t *order, int count,
+                           int32_t *next, uint64_t *scratch, int64_t max_rows, int64_t ldS, int grid);
+size_t batched_scratch_words(int64_t max_rows, int64_t ldS, int grid);
+size_t batched_smem_bytes();
+int batched_grid(int num_sms);
 cudaError_t launch_solve_check(cudaStream_t st, const uint64_t *Aug, int64_t ldaug, int64_t n,
                                int64_t wa, int64_t wb, const int64_t *r_dev, int32_t *flag);
 cudaError_t launch_solve_finish(cudaStream_t st, const uint64_t *Aug, int64_t ldaug, int64_t n,

@@ -30,28 +30,9 @@
 // by ballot at the end.  The window is exact whenever every pivot column
 // finds its row inside it (or it holds all remaining rows).  Otherwise the
 // block-wide path redoes the stripe over all remaining rows.
-#include "common.cuh"
-
-#include <climits>
+#include "panel_dev.cuh"
 
 namespace gf2 {
-
-// Transpose a 32 x 32 bit block held one row per lane (bit c of lane r =
-// entry (r, c)) so that lane c receives column c (bit r = entry (r, c)):
-// five rounds of swapping the off-diagonal sub-blocks of size 16, 8, 4, 2, 1.
-__device__ __forceinline__ unsigned transpose32(unsigned x)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int j = 16 >> k;
-        const unsigned m = masks[k];
-        const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
-        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
-    }
-    return x;
-}
 
 __global__ void init_ple_kernel(int64_t *P, int64_t *Q, int64_t m, int64_t qn, int32_t *map,
                                 int64_t *r_dev)
@@ -81,15 +62,7 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
              StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
              PanelScratch gs, int32_t *fallbacks)
 {
-    __shared__ uint64_t sh_E[KS], sh_L[KS];
-    __shared__ int32_t sh_t[KS];
-    __shared__ uint8_t sh_j[KS];
-    __shared__ int32_t sh_Soff[SMAX];
-    __shared__ int64_t sh_Ssrc[SMAX];
-    __shared__ int32_t sh_perm[PANEL_WIN];
-    __shared__ int sh_fail, sh_rbar, sh_nS, sh_maxpos, sh_best;
-    __shared__ unsigned long long sh_colmask;
-
+    __shared__ PanelShared sh;
     StripeDesc *d = descs + s;
     const int64_t r = *r_dev;
     const int c = s * KS;
@@ -104,204 +77,21 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         }
         return;
     }
-    // ---------------- fast path: one warp, bit-sliced window of up to 128 rows
-    if (warp == 0) {
-        const int Wn = (int)min(rows, (int64_t)PANEL_WIN);
-        // load: lane l holds window rows l, l+32, l+64, l+96 ...
-        uint64_t rw[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int sl = b * 32 + lane;
-            rw[b] = (sl < Wn) ? A[(r + sl) * ld + cw] : 0ull;
-        }
-        // ... transposed so that lane l owns columns l and l+32 as 128-row masks
-        uint64_t c0lo, c0hi, c1lo, c1hi;
-        {
-            unsigned t0[4], t1[4];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                t0[b] = transpose32((unsigned)rw[b]);
-                t1[b] = transpose32((unsigned)(rw[b] >> 32));
-            }
-            c0lo = ((uint64_t)t0[1] << 32) | t0[0];
-            c0hi = ((uint64_t)t0[3] << 32) | t0[2];
-            c1lo = ((uint64_t)t1[1] << 32) | t1[0];
-            c1hi = ((uint64_t)t1[3] << 32) | t1[2];
-        }
-        for (int x = lane; x < PANEL_WIN; x += 32) sh_perm[x] = x;
-        __syncwarp();
-        // L columns (pivot p's column = rows eliminated by it), lane owns p = lane, lane + 32
-        uint64_t l0lo = 0, l0hi = 0, l1lo = 0, l1hi = 0;
-        int p = 0, tmax = -1;
-        bool fail = false;
-        for (int j = 0; j < keff && p < Wn; ++j) {
-            const int owner = j & 31;
-            uint64_t jlo = __shfl_sync(0xffffffffu, (j < 32) ? c0lo : c1lo, owner);
-            uint64_t jhi = __shfl_sync(0xffffffffu, (j < 32) ? c0hi : c1hi, owner);
-            const uint64_t ge_lo = (p < 64) ? (~0ull << p) : 0ull;
-            const uint64_t ge_hi = (p < 64) ? ~0ull : (~0ull << (p - 64));
-            const uint64_t clo = jlo & ge_lo, chi = jhi & ge_hi;
-            int t;
-            if (clo) t = __ffsll((long long)clo) - 1;
-            else if (chi) t = 64 + __ffsll((long long)chi) - 1;
-            else {
-                if (Wn < rows) { fail = true; break; }   // the pivot may lie outside the window
-                continue;                                // column j has no pivot
-            }
-            // exchange rows p and t in every 128-row mask
-            const uint64_t mp_lo = (p < 64) ? (1ull << p) : 0ull, mp_hi = (p < 64) ? 0ull : (1ull << (p - 64));
-            const uint64_t mt_lo = (t < 64) ? (1ull << t) : 0ull, mt_hi = (t < 64) ? 0ull : (1ull << (t - 64));
-            const uint64_t both_lo = mp_lo | mt_lo, both_hi = mp_hi | mt_hi;
-#define GF2_SWAPROWS(lo, hi)                                                        \
-            do {                                                                    \
-                const bool d_ = (((lo) & mp_lo) | ((hi) & mp_hi)) != 0ull;          \
-                const bool e_ = (((lo) & mt_lo) | ((hi) & mt_hi)) != 0ull;          \
-                if (d_ != e_) { (lo) ^= both_lo; (hi) ^= both_hi; }                 \
-            } while (0)
-            GF2_SWAPROWS(jlo, jhi);
-            const uint64_t gt_lo = (p >= 63) ? 0ull : (~0ull << (p + 1));
-            const uint64_t gt_hi = (p < 63) ? ~0ull : ((p - 63) >= 64 ? 0ull : (~0ull << (p - 63)));
-            const uint64_t rlo = jlo & gt_lo, rhi = jhi & gt_hi;   // rows below p holding column j
-            GF2_SWAPROWS(c0lo, c0hi);
-            GF2_SWAPROWS(c1lo, c1hi);
-            GF2_SWAPROWS(l0lo, l0hi);
-            GF2_SWAPROWS(l1lo, l1hi);
-#undef GF2_SWAPROWS
-            // the pivot row's entry in each owned column decides whether it is added
-            if (((c0lo & mp_lo) | (c0hi & mp_hi)) != 0ull) { c0lo ^= rlo; c0hi ^= rhi; }
-            if (((c1lo & mp_lo) | (c1hi & mp_hi)) != 0ull) { c1lo ^= rlo; c1hi ^= rhi; }
-            if (lane == (p & 31)) {
-                if (p < 32) { l0lo = rlo; l0hi = rhi; } else { l1lo = rlo; l1hi = rhi; }
-            }
-            if (lane == 0) {
-                sh_t[p] = t;
-                sh_j[p] = (uint8_t)j;
-                const int a = sh_perm[p];
-                sh_perm[p] = sh_perm[t];
-                sh_perm[t] = a;
-            }
-            tmax = max(tmax, t);
-            ++p;
-        }
-        if (!fail) {
-            // rows 0..p-1 of the window now hold the pivots: transpose the column
-            // masks back into rows (lane r gets rows r and r + 32)
-            {
-                const unsigned e00 = transpose32((unsigned)c0lo), e01 = transpose32((unsigned)c1lo);
-                const unsigned e10 = transpose32((unsigned)(c0lo >> 32)), e11 = transpose32((unsigned)(c1lo >> 32));
-                const unsigned f00 = transpose32((unsigned)l0lo), f01 = transpose32((unsigned)l1lo);
-                const unsigned f10 = transpose32((unsigned)(l0lo >> 32)), f11 = transpose32((unsigned)(l1lo >> 32));
-                const int q0 = lane, q1 = lane + 32;
-                if (q0 < p) {
-                    sh_E[q0] = ((uint64_t)e01 << 32) | e00;
-                    sh_L[q0] = ((((uint64_t)f01 << 32) | f00)) & ((q0 == 0) ? 0ull : (~0ull >> (64 - q0)));
-                }
-                if (q1 < p) {
-                    sh_E[q1] = ((uint64_t)e11 << 32) | e10;
-                    sh_L[q1] = ((((uint64_t)f11 << 32) | f10)) & (~0ull >> (64 - q1));
-                }
-            }
-            __syncwarp();
-            // staged rows: pivot rows first, then rows displaced into [p, tmax]
-            for (int k = lane; k < p; k += 32) { sh_Soff[k] = k; sh_Ssrc[k] = r + sh_perm[k]; }
-            int base = p;
-            for (int b0 = p; b0 <= tmax; b0 += 32) {
-                const int sl = b0 + lane;
-                const bool mv = sl <= tmax && sh_perm[sl] != sl;
-                const unsigned bm = __ballot_sync(0xffffffffu, mv);
-                if (mv) {
-                    const int k = base + __popc(bm & ((1u << lane) - 1u));
-                    sh_Soff[k] = sl;
-                    sh_Ssrc[k] = r + sh_perm[sl];
-                }
-                base += __popc(bm);
-            }
-            if (lane == 0) { sh_nS = base; sh_maxpos = max(p - 1, tmax); }
-        }
-        if (lane == 0) { sh_fail = fail ? 1 : 0; sh_rbar = p; }
-    }
+    if (warp == 0) panel_window(A, r, ld, cw, rows, keff, sh);
     __syncthreads();
-
-    // ---------------- block-wide path over all remaining rows
-    if (sh_fail) {
-        const int nthr = blockDim.x;
-        if (tid == 0) { sh_colmask = 0; if (fallbacks) atomicAdd(fallbacks, 1); }
-        __syncthreads();
-        unsigned long long orv = 0;
-        for (int64_t sl = tid; sl < rows; sl += nthr) {
-            const uint64_t v = A[(r + sl) * ld + cw];
-            gs.val[sl] = v;
-            gs.lb[sl] = 0;
-            gs.src[sl] = (int32_t)sl;
-            orv |= v;
-        }
-        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)orv);
-        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(orv >> 32));
-        if (lane == 0) atomicOr(&sh_colmask, ((unsigned long long)hi << 32) | lo);
-        __syncthreads();
-        // a column that is zero in every remaining row stays zero in every
-        // combination of them, so it can never hold a pivot
-        const uint64_t colmask = sh_colmask;
-        int p = 0, tmax = -1;
-        for (int j = 0; j < keff && p < rows; ++j) {
-            if (!((colmask >> j) & 1ull)) continue;
-            __syncthreads();
-            if (tid == 0) sh_best = INT_MAX;
-            __syncthreads();
-            for (int64_t base = p; base < rows; base += nthr) {
-                const int64_t sl = base + tid;
-                const bool hit = sl < rows && ((gs.val[sl] >> j) & 1ull);
-                if (__syncthreads_or(hit)) {
-                    if (hit) atomicMin(&sh_best, (int)sl);
-                    __syncthreads();
-                    break;
-                }
-            }
-            const int t = sh_best;
-            if (t == INT_MAX) continue;
-            __syncthreads();
-            if (tid == 0) {
-                const uint64_t tv = gs.val[t], tl = gs.lb[t];
-                const int32_t ts = gs.src[t];
-                gs.val[t] = gs.val[p]; gs.lb[t] = gs.lb[p]; gs.src[t] = gs.src[p];
-                gs.val[p] = tv; gs.lb[p] = tl; gs.src[p] = ts;
-                sh_t[p] = t; sh_j[p] = (uint8_t)j; sh_E[p] = tv; sh_L[p] = tl;
-            }
-            __syncthreads();
-            const uint64_t pv = sh_E[p];
-            const uint64_t bitp = 1ull << p;
-            for (int64_t sl = p + 1 + tid; sl < rows; sl += nthr) {
-                const uint64_t v = gs.val[sl];
-                if ((v >> j) & 1ull) { gs.val[sl] = v ^ pv; gs.lb[sl] |= bitp; }
-            }
-            tmax = max(tmax, t);
-            ++p;
-        }
-        __syncthreads();
-        if (tid == 0) { sh_rbar = p; sh_nS = p; sh_maxpos = max(p - 1, tmax); }
-        for (int k = tid; k < p; k += nthr) { sh_Soff[k] = k; sh_Ssrc[k] = r + gs.src[k]; }
-        __syncthreads();
-        for (int64_t sl = p + tid; sl <= tmax; sl += nthr) {
-            if (gs.src[sl] != (int32_t)sl) {
-                const int k = atomicAdd(&sh_nS, 1);
-                sh_Soff[k] = (int32_t)sl;
-                sh_Ssrc[k] = r + gs.src[sl];
-            }
-        }
-        __syncthreads();
-    }
+    if (sh.fail) panel_block(A, r, ld, cw, rows, keff, gs, sh, fallbacks);
 
     // ---------------- outputs
-    const int rbar = sh_rbar;
+    const int rbar = sh.rbar;
     if (warp == 1) {
         // U11^-1 for the RREF recovery, U11[p][q] = E11[p] at column qbar[q]
         // (unit upper triangular): lane-parallel backward substitution per
         // column, rows collected by ballot.  Runs beside warp 0's L11^-1.
         __shared__ uint64_t sU[KS];
         for (int p = lane; p < rbar; p += 32) {
-            const uint64_t e = sh_E[p];
+            const uint64_t e = sh.E[p];
             uint64_t u = 0;
-            for (int q = 0; q < rbar; ++q) u |= ((e >> sh_j[q]) & 1ull) << q;
+            for (int q = 0; q < rbar; ++q) u |= ((e >> sh.j[q]) & 1ull) << q;
             sU[p] = u;
         }
         __syncwarp();
@@ -317,37 +107,23 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
             if (lane == 0) d->Minv[p] = ((uint64_t)hi << 32) | lo;
         }
     }
-    if (warp == 0) {
-        // L11^-1 column by column (lane owns columns lane and lane + 32):
-        // forward substitution L x = e_col, then rows by ballot.
-        uint64_t x0 = 0, x1 = 0;
-        for (int p = 0; p < rbar; ++p) {
-            const uint64_t Lp = sh_L[p];
-            x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(Lp & x0)) & 1) << p;
-            x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(Lp & x1)) & 1) << p;
-        }
-        for (int p = 0; p < rbar; ++p) {
-            const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
-            const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
-            if (lane == 0) d->Linv[p] = ((uint64_t)hi << 32) | lo;
-        }
-    }
+    if (warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv);
     for (int p = tid; p < rbar; p += blockDim.x) {
-        P[r + p] = r + sh_t[p];
-        Q[r + p] = c + sh_j[p];
-        d->E11[p] = sh_E[p];
-        d->L11[p] = sh_L[p];
-        d->qbar[p] = sh_j[p];
+        P[r + p] = r + sh.t[p];
+        Q[r + p] = c + sh.j[p];
+        d->E11[p] = sh.E[p];
+        d->L11[p] = sh.L[p];
+        d->qbar[p] = sh.j[p];
     }
-    const int nS = sh_nS;
+    const int nS = sh.nS;
     for (int k = tid; k < nS; k += blockDim.x) {
-        d->S_off[k] = sh_Soff[k];
-        d->S_src[k] = sh_Ssrc[k];
-        map[r + sh_Soff[k]] = s * 256 + k;
+        d->S_off[k] = sh.Soff[k];
+        d->S_src[k] = sh.Ssrc[k];
+        map[r + sh.Soff[k]] = s * 256 + k;
     }
     if (tid == 0) {
-        d->r = r; d->rbar = rbar; d->c = c; d->nS = nS; d->maxpos = sh_maxpos;
-        d->tier = sh_fail ? 2 : 1;
+        d->r = r; d->rbar = rbar; d->c = c; d->nS = nS; d->maxpos = sh.maxpos;
+        d->tier = sh.fail ? 2 : 1;
         *r_dev = r + rbar;
     }
 }

@@ -214,22 +214,52 @@ def test_solve(h, n, nrhs, kind):
 
 # -------------------------------------------------------------------- batched
 
-def test_ple_batched_matches_single(h):
+def _batched_check(h, mats):
+    """Run gf2_ple_batched on [(A, m, n, ld_extra)] and compare each with the oracle."""
+    import concurrent.futures as cf
     import torch
-    specs = gi.batch_recipe(count=24)
-    items, refs = [], []
-    for sp in specs:
-        A = gi.batch_matrix(sp)
-        m, n = sp["m"], sp["n"]
-        dA = to_dev(A)
+    items = []
+    for A, m, n, extra in mats:
+        dA = to_dev(A, gi.words_for(n) + extra) if m > 0 else torch.zeros((1, 1), dtype=torch.int64,
+                                                                           device="cuda")
         items.append((dA, m, n, vec_dev(m), vec_dev(min(m, n)), vec_dev(1)))
-        refs.append(ref_ple(A, m, n))
     h.ple_batched(items)
     torch.cuda.synchronize()
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        refs = list(ex.map(lambda t: ref_ple_1(t[0], t[1], t[2]), mats))
     for (dA, m, n, P, Q, rk), want in zip(items, refs):
-        got = (int(rk.cpu()[0]), to_host(dA, gi.words_for(n)), P.cpu().numpy()[:m],
-               Q.cpu().numpy()[:min(m, n)])
+        got = (int(rk.cpu()[0]), to_host(dA, gi.words_for(n)) if m > 0 and n > 0 else want[1],
+               P.cpu().numpy()[:m], Q.cpu().numpy()[:min(m, n)])
         assert_ple_equal(got, want)
+
+
+def ref_ple_1(A, m, n):
+    B = A.copy()
+    r, P, Q = oracle.ple(B, m, n, threads=1)
+    return r, B, P, Q
+
+
+def test_ple_batched_matches_oracle_small(h):
+    specs = gi.batch_recipe(count=24)
+    _batched_check(h, [(gi.batch_matrix(sp), sp["m"], sp["n"], 0) for sp in specs])
+
+
+def test_ple_batched_workload_4096(h):
+    """The batched workload: 4096 matrices, sides uniform in 64..1024, 25% with
+    10% of rows zeroed; every result bit-exact against the oracle."""
+    specs = gi.batch_recipe(count=4096)
+    _batched_check(h, [(gi.batch_matrix(sp), sp["m"], sp["n"], 0) for sp in specs])
+
+
+def test_ple_batched_mixed_sizes_and_edges(h):
+    mats = [(make("dense", 5000, 300, 1), 5000, 300, 0),        # beyond the batched kernel
+            (make("lastrow_pivot", 1500, 200, 2), 1500, 200, 0),  # block-wide panel inside a CTA
+            (make("sparse", 700, 900, 3), 700, 900, 1),          # odd leading dimension
+            (make("dense", 1, 1, 4), 1, 1, 0),
+            (make("zeros", 64, 64, 5), 64, 64, 0),
+            (np.zeros((3, 1), np.uint64), 3, 0, 0),              # no columns
+            (np.zeros((0, 1), np.uint64), 0, 5, 0)]              # no rows
+    _batched_check(h, mats)
 
 
 # ------------------------------------------------------------ host-buffer API
