@@ -246,6 +246,70 @@ def bench_batched(h, torch, dev, stream, reps: int = 5):
             "plain_ms": t_plain, "speedup_vs_plain": t_plain / t, "launches": 1}
 
 
+def bench_served(h, torch, dev, rates=(200, 1000, 5000), jobs_per_rate=400, pool_size=48, slots=6):
+    """The served solve workload: Poisson arrivals of gf2_solve jobs (n
+    log-uniform in 128..16384, 1..64 right-hand sides) through the
+    continuous-batching server, against the plain path (one job at a time
+    through one handle) on the same arrivals.  Inputs come from a pool of
+    pre-generated jobs reused in arrival order."""
+    import gf2inputs as gi
+    import paper_1111_6549_gb300 as g
+    pool = []
+    for jb in gi.solve_stream_recipe(pool_size, rate=1.0):
+        A, B = gi.solve_job_inputs(jb)
+        n, nrhs = jb["n"], jb["nrhs"]
+        Ap = torch.from_numpy(A.view(np.int64)).pin_memory()
+        Bp = torch.from_numpy(B.view(np.int64)).pin_memory()
+        Xp = torch.zeros_like(Bp).pin_memory()
+        pool.append((n, nrhs, Ap, Bp, Xp))
+    max_n = max(p[0] for p in pool)
+    out = {"workload": "Poisson arrivals of solve jobs, n log-uniform 128..16384, nrhs U{1..64}",
+           "slots": slots, "pool": pool_size, "rates": []}
+    srv = g.Server(slots=slots, max_n=max_n, max_nrhs=64)
+    # device buffers for the plain path
+    dA = torch.empty((max_n, gi.words_for(max_n)), dtype=torch.int64, device=dev)
+    dB = torch.empty((max_n, 1), dtype=torch.int64, device=dev)
+    for rate in rates:
+        arr = gi.solve_stream_recipe(jobs_per_rate, rate=float(rate), seed=gi.BASE_SEED + 4 + rate)
+        t0 = g.Server.clock() + 0.01
+        for k, jb in enumerate(arr):
+            n, nrhs, Ap, Bp, Xp = pool[k % pool_size]
+            while g.Server.clock() < t0 + jb["t"]:
+                pass
+            srv.submit(k, Ap, n, Bp, nrhs, Xp)
+        srv.drain()
+        res = srv.poll(jobs_per_rate + 8)
+        lat = sorted((r[5] - r[3]) * 1e3 for r in res)
+        span = max(r[5] for r in res) - min(r[3] for r in res)
+        # plain path: one job at a time, same arrivals
+        lat_p, t_first, t_last = [], None, None
+        t0 = g.Server.clock() + 0.01
+        for k, jb in enumerate(arr):
+            n, nrhs, Ap, Bp, Xp = pool[k % pool_size]
+            ta = t0 + jb["t"]
+            while g.Server.clock() < ta:
+                pass
+            now = g.Server.clock()
+            t_first = now if t_first is None else t_first
+            a = dA[:n, :gi.words_for(n)]
+            b = dB[:n, :1]
+            a.copy_(Ap, non_blocking=True)
+            b.copy_(Bp, non_blocking=True)
+            h.solve(a, b, n, nrhs)
+            Xp.copy_(b.cpu())
+            t_last = g.Server.clock()
+            lat_p.append((t_last - ta) * 1e3)
+        lat_p.sort()
+        q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))]
+        out["rates"].append({"rate_per_s": rate, "jobs": len(res),
+                             "served": {"p50_ms": q(lat, 0.5), "p99_ms": q(lat, 0.99),
+                                        "jobs_per_s": len(res) / span},
+                             "plain": {"p50_ms": q(lat_p, 0.5), "p99_ms": q(lat_p, 0.99),
+                                       "jobs_per_s": len(lat_p) / (t_last - t_first)}})
+    srv.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import gf2inputs as gi
@@ -407,6 +471,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and not args.no_batch:
         batched = bench_batched(h, torch, dev, stream)
+    served = None
+    if rank == 0 and not args.no_serve:
+        served = bench_served(h, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -422,7 +489,7 @@ def run_ours(args):
                            "l2": "inputs (512 MiB) larger than L2; fresh copy restored before each step",
                            "seconds_per_step": max_ms / args.steps / 1e3,
                            "ple_only_ms": ple_ms, "side_32768": side},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "served": served,
                 "gpu_launches": st["kernel_launches"], "clocks": clk.summary(),
                 "panel_fallbacks": st["panel_fallbacks"], "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
@@ -441,6 +508,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -119,6 +119,10 @@ int gf2_mul(gf2_handle_t handle, uint64_t *C, int64_t ldc, const uint64_t *A, in
  */
 int gf2_solve(gf2_handle_t handle, uint64_t *A, int64_t n, int64_t lda, uint64_t *B,
               int64_t nrhs, int64_t ldb, int *solve_status);
+/* As gf2_solve, but the status goes to DEVICE memory status_dev (one int32)
+ * and nothing waits. */
+int gf2_solve_async(gf2_handle_t handle, uint64_t *A, int64_t n, int64_t lda, uint64_t *B,
+                    int64_t nrhs, int64_t ldb, int32_t *status_dev);
 
 /*
  * Many independent PLE decompositions (each exactly as gf2_ple).  Matrices
@@ -171,6 +175,49 @@ int gf2_rref_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_
  */
 int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_words, int64_t *P, int64_t *Q,
                     int64_t *rank, void *stream);
+
+/*
+ * Continuous-batching solve server.  Solving dense systems is the use the
+ * paper gives the decomposition (Section 1); serving many of them is this
+ * library's: a worker thread owns `slots` execution slots (stream, handle,
+ * device buffers for systems up to max_n x max_n with up to max_nrhs right-
+ * hand sides, all allocated and sized at creation).  Submitted jobs queue in
+ * arrival order; the head of the queue is admitted whenever a slot is free
+ * and its device footprint fits in hbm_budget_bytes (0: no limit), so jobs
+ * that arrive while others run are started at once and overlap them on the
+ * device.  Results (status as gf2_solve, timestamps on gf2_server_clock)
+ * are collected with gf2_server_poll.
+ *   Job buffers A (n x n, lda), B (n x nrhs, ldb) and X (n x nrhs, ldx) are
+ *   HOST pointers (pinned memory recommended) owned by the caller, who must
+ *   keep them alive and unmodified until the job's result is polled.
+ */
+typedef struct gf2_server *gf2_server_t;
+typedef struct gf2_solve_job {
+    uint64_t id;
+    const uint64_t *A;
+    int64_t n, lda;
+    const uint64_t *B;
+    int64_t nrhs, ldb;
+    uint64_t *X;
+    int64_t ldx;
+} gf2_solve_job;
+typedef struct gf2_solve_result {
+    uint64_t id;
+    int status;      /* GF2_SOLVE_*, or -1 when error != 0 */
+    int error;       /* GF2_OK or a GF2_E* code */
+    double t_submit, t_start, t_done;
+} gf2_solve_result;
+int gf2_server_create(gf2_server_t *server, int device, int slots, int64_t max_n, int64_t max_nrhs,
+                      size_t hbm_budget_bytes);
+int gf2_server_submit(gf2_server_t server, const gf2_solve_job *job);
+/* Move up to max_results finished jobs into out; *count receives how many. */
+int gf2_server_poll(gf2_server_t server, gf2_solve_result *out, int max_results, int *count);
+/* Wait until every submitted job has finished. */
+int gf2_server_drain(gf2_server_t server);
+/* The server's clock, in seconds (monotonic). */
+double gf2_server_clock(void);
+/* Finish every queued job, then stop the worker and free everything. */
+int gf2_server_destroy(gf2_server_t server);
 
 /* Counters of the work enqueued since the last reset (host struct). */
 typedef struct gf2_stats {

@@ -41,6 +41,17 @@ class _Stats(ctypes.Structure):
                 ("other_ms", ctypes.c_double)]
 
 
+class SolveJob(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("A", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("nrhs", ctypes.c_int64),
+                ("ldb", ctypes.c_int64), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("error", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class Desc(ctypes.Structure):
     """gf2_desc of the batched entry point."""
     _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
@@ -88,6 +99,15 @@ def load():
             "gf2_get_stats": ([vp, ctypes.POINTER(_Stats)], ctypes.c_int),
             "gf2_reset_stats": ([vp], ctypes.c_int),
             "gf2_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "gf2_solve_async": ([vp, vp, i64, i64, vp, i64, i64, vp], ctypes.c_int),
+            "gf2_server_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, i64, i64, ctypes.c_size_t],
+                                  ctypes.c_int),
+            "gf2_server_submit": ([vp, ctypes.POINTER(SolveJob)], ctypes.c_int),
+            "gf2_server_poll": ([vp, ctypes.POINTER(SolveResult), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                                ctypes.c_int),
+            "gf2_server_drain": ([vp], ctypes.c_int),
+            "gf2_server_clock": ([], ctypes.c_double),
+            "gf2_server_destroy": ([vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -216,6 +236,13 @@ class Handle:
         self._bind_stream()
         _check(load().gf2_ple_batched(self._h, arr, len(items)), "gf2_ple_batched")
 
+    def solve_async(self, A, B, n: int, nrhs: int, status_dev) -> None:
+        lda = _mat(A, n, n)
+        ldb = _mat(B, n, nrhs) if nrhs > 0 else 1
+        self._bind_stream()
+        _check(load().gf2_solve_async(self._h, _dptr(A), n, lda, _dptr(B) if nrhs else None, nrhs, ldb,
+                                      _dptr(status_dev)), "gf2_solve_async")
+
     def workspace_bytes(self, m: int, n: int) -> int:
         return int(load().gf2_workspace_bytes(self._h, m, n))
 
@@ -288,3 +315,58 @@ def ple_noalloc(A, m: int, n: int, P, Q) -> int:
     _check(f(_dptr(A), m, n, ld, _dptr(P), _dptr(Q), ctypes.byref(rank), ctypes.c_void_p(s)),
            "gf2_ple_noalloc")
     return rank.value
+
+
+class Server:
+    """gf2_server: continuous-batching solve server (native worker thread).
+
+    Jobs are host buffers (numpy uint64 arrays or pinned CPU torch tensors);
+    the caller keeps them alive until the job's result has been polled.
+    """
+
+    def __init__(self, slots: int = 4, max_n: int = 16384, max_nrhs: int = 64,
+                 hbm_budget_bytes: int = 0, device: int | None = None):
+        import torch
+        L = load()
+        dev = torch.cuda.current_device() if device is None else device
+        s = ctypes.c_void_p()
+        _check(L.gf2_server_create(ctypes.byref(s), dev, slots, max_n, max_nrhs, hbm_budget_bytes),
+               "gf2_server_create")
+        self._s = s
+
+    @staticmethod
+    def _host(a):
+        if isinstance(a, np.ndarray):
+            return a.ctypes.data, a.shape[1] if a.ndim == 2 else 1
+        return a.data_ptr(), a.stride(0)
+
+    def submit(self, job_id: int, A, n: int, B, nrhs: int, X) -> None:
+        pa, lda = self._host(A)
+        pb, ldb = self._host(B)
+        px, ldx = self._host(X)
+        j = SolveJob(job_id, pa, n, lda, pb, nrhs, ldb, px, ldx)
+        _check(load().gf2_server_submit(self._s, ctypes.byref(j)), "gf2_server_submit")
+
+    def poll(self, max_results: int = 4096):
+        buf = (SolveResult * max_results)()
+        cnt = ctypes.c_int(0)
+        _check(load().gf2_server_poll(self._s, buf, max_results, ctypes.byref(cnt)), "gf2_server_poll")
+        return [(r.id, r.status, r.error, r.t_submit, r.t_start, r.t_done) for r in buf[:cnt.value]]
+
+    def drain(self) -> None:
+        _check(load().gf2_server_drain(self._s), "gf2_server_drain")
+
+    @staticmethod
+    def clock() -> float:
+        return float(load().gf2_server_clock())
+
+    def close(self) -> None:
+        if getattr(self, "_s", None):
+            load().gf2_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -50,6 +50,7 @@ constexpr size_t SM_ERR = 8;       // int32 internal-check flag
 constexpr size_t SM_FALLBACK = 12; // int32 block-wide panel count
 constexpr size_t SM_BYTES = 16;    // uint64 algorithmic bytes of update launches
 constexpr size_t SM_FLAG = 24;     // int32 solve inconsistency flag
+constexpr size_t SM_STATUS = 28;   // int32 solve status
 constexpr size_t SM_BYTES_TOTAL = 256;
 
 int64_t *r_dev(gf2_handle *h) { return reinterpret_cast<int64_t *>(h->small + SM_RANK); }
@@ -543,23 +544,17 @@ int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t
     return GF2_OK;
 }
 
-int gf2_solve(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, int64_t nrhs, int64_t ldb,
-              int *solve_status)
+// Enqueue a solve; the status (GF2_SOLVE_*) is written to device memory.
+static int solve_enqueue(gf2_handle *h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, int64_t nrhs,
+                         int64_t ldb, int32_t *status_dev)
 {
-    int rc = check_args(h, A, n, n, lda);
-    if (rc) return rc;
-    if (!solve_status || nrhs < 0) return GF2_EINVAL;
-    if (n > 0 && nrhs > 0 && (!B || ldb < words_for(nrhs))) return GF2_EINVAL;
-    DeviceGuard g(h->device);
-    *solve_status = GF2_SOLVE_UNIQUE;
-    if (n == 0) return GF2_OK;
     const int64_t wa = words_for(n);
     const int64_t wb = std::max<int64_t>(words_for(nrhs), 1);
     int64_t ldaug = wa + wb;
     ldaug += ldaug & 1;
     const int64_t ncols = 64 * (wa + wb);
     const size_t aug_bytes = align256((size_t)n * ldaug * 8);
-    rc = grow(&h->io, &h->io_cap, aug_bytes, h->stream);
+    int rc = grow(&h->io, &h->io_cap, aug_bytes, h->stream);
     if (rc) return rc;
     const Layout L = layout_for(n, ncols);
     rc = grow(&h->ws, &h->ws_cap, L.total, h->stream);
@@ -586,13 +581,44 @@ int gf2_solve(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, 
         CK(launch_solve_finish(h->stream, Aug, ldaug, n, wa, words_for(nrhs), r_dev(h), Q, B, ldb));
         h->launches += 2;
     }
-    int64_t rank = 0;
-    int32_t flag = 0;
-    CK(cudaMemcpyAsync(&rank, r_dev(h), 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(&flag, flag_dev(h), 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(launch_solve_status(h->stream, r_dev(h), flag_dev(h), n, status_dev));
+    h->launches += 1;
+    return GF2_OK;
+}
+
+int gf2_solve_async(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, int64_t nrhs,
+                    int64_t ldb, int32_t *status_dev)
+{
+    int rc = check_args(h, A, n, n, lda);
+    if (rc) return rc;
+    if (!status_dev || nrhs < 0) return GF2_EINVAL;
+    if (n > 0 && nrhs > 0 && (!B || ldb < words_for(nrhs))) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    if (n == 0) {
+        CK(cudaMemsetAsync(status_dev, 0, sizeof(int32_t), h->stream));
+        return GF2_OK;
+    }
+    return solve_enqueue(h, A, n, lda, B, nrhs, ldb, status_dev);
+}
+
+int gf2_solve(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, int64_t nrhs, int64_t ldb,
+              int *solve_status)
+{
+    int rc = check_args(h, A, n, n, lda);
+    if (rc) return rc;
+    if (!solve_status || nrhs < 0) return GF2_EINVAL;
+    if (n > 0 && nrhs > 0 && (!B || ldb < words_for(nrhs))) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    *solve_status = GF2_SOLVE_UNIQUE;
+    if (n == 0) return GF2_OK;
+    int32_t *status_dev = reinterpret_cast<int32_t *>(h->small + SM_STATUS);
+    rc = solve_enqueue(h, A, n, lda, B, nrhs, ldb, status_dev);
+    if (rc) return rc;
+    int32_t st = 0;
+    CK(cudaMemcpyAsync(&st, status_dev, 4, cudaMemcpyDeviceToHost, h->stream));
     rc = finish_sync(h);
     if (rc) return rc;
-    *solve_status = flag ? GF2_SOLVE_INCONSISTENT : (rank == n ? GF2_SOLVE_UNIQUE : GF2_SOLVE_UNDERDETERMINED);
+    *solve_status = st;
     return GF2_OK;
 }
 

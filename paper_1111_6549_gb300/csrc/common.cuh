@@ -102,6 +102,8 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
+cudaError_t launch_solve_status(cudaStream_t st, const int64_t *r_dev, const int32_t *flag, int64_t n,
+                                int32_t *status);
 cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const int32_t *order, int count,
                            int32_t *next, uint64_t *scratch, int64_t max_rows, int64_t ldS, int grid);
 size_t batched_scratch_words(int64_t max_rows, int64_t ldS, int grid);

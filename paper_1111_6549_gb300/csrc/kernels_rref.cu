@@ -167,4 +167,16 @@ cudaError_t launch_solve_finish(cudaStream_t st, const uint64_t *Aug, int64_t ld
     return cudaGetLastError();
 }
 
+__global__ void solve_status_kernel(const int64_t *r_dev, const int32_t *flag, int64_t n, int32_t *status)
+{
+    *status = *flag ? 2 : (*r_dev == n ? 0 : 1);
+}
+
+cudaError_t launch_solve_status(cudaStream_t st, const int64_t *r_dev, const int32_t *flag, int64_t n,
+                                int32_t *status)
+{
+    solve_status_kernel<<<1, 1, 0, st>>>(r_dev, flag, n, status);
+    return cudaGetLastError();
+}
+
 }  // namespace gf2
