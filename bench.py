@@ -135,6 +135,16 @@ def dist_setup(n_gpus: int):
     return world, rank, local, pg
 
 
+def max_over_ranks(value: float, pg) -> float:
+    """The step time every rank reports is the slowest rank's (gloo all-reduce MAX)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t[0])
+
+
 def oracle_sample(A: np.ndarray, m: int, n: int, pivots: int, threads: int):
     """Time the oracle's first `pivots` elimination steps over the full width."""
     import oracle
@@ -161,9 +171,9 @@ def cpu_baseline(A: np.ndarray, m: int, n: int, target_s: float = 12.0):
 def run_reference(args):
     world, rank, local, pg = dist_setup(args.gpus)
     if rank != 0:
-        return 0
+        return 0                      # the CPU reference runs on rank 0 only
     import gf2inputs as gi
-    m = n = N_MAIN
+    m = n = args.n
     A = gi.dense_square(n)
     threads = os.cpu_count() or 1
     _, dt1, k1 = oracle_sample(A, m, n, 16, threads)
@@ -371,11 +381,7 @@ def run_ours(args):
     sd = h.stats()
     h.set_profiling(0)
     per_step_ms = ms / args.steps
-    max_ms = ms
-    if pg:
-        t = torch.tensor([ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        max_ms = float(t[0])
+    max_ms = max_over_ranks(ms, pg)
     W_bits = work_bits(m, n, r)
     value = world * args.steps * W_bits / (max_ms / 1e3) / 1e9
 
@@ -503,7 +509,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--size", dest="n", type=int, default=N_MAIN)
     ap.add_argument("--no-side", dest="side", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
