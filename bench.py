@@ -205,6 +205,7 @@ def bench_batched(h, torch, dev, stream, reps: int = 5):
     with 10% of rows zeroed) in one gf2_ple_batched call, against the plain
     path (one gf2_ple_async per matrix) on the same GPU."""
     import gf2inputs as gi
+    import paper_1111_6549_gb300 as g
     specs = gi.batch_recipe(count=4096)
     mats = [gi.batch_matrix(sp) for sp in specs]
     offs, tot = [], 0
@@ -224,18 +225,35 @@ def bench_batched(h, torch, dev, stream, reps: int = 5):
     for b, (sp, o, A) in enumerate(zip(specs, offs, mats)):
         items.append((work[o:o + A.size].view(A.shape[0], A.shape[1]), sp["m"], sp["n"], P[b], Q[b],
                       R[b:b + 1]))
-    work.copy_(pristine)
-    h.ple_batched(items)                                  # warm-up
-    times = []
-    for _ in range(reps):
+    def timed(fn):
         work.copy_(pristine)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        h.ple_batched(items)
-        b.record(stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-    t = statistics.median(times)
+        fn()                                              # warm-up
+        times = []
+        for _ in range(reps):
+            work.copy_(pristine)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        return statistics.median(times)
+
+    # the C-ABI call with its descriptor array built once (building 4096
+    # ctypes descriptors in Python would otherwise dominate the timed region)
+    lib, descs = g.load(), h._descs(items)
+    h._bind_stream()
+
+    def direct():
+        rc = lib.gf2_ple_batched(h._h, descs, len(items))
+        assert rc == 0, rc
+
+    t_default = timed(direct)                             # default configuration in every class
+    chosen, tune_ms = h.batched_autotune(reps=3)          # per size class, on separate seeded batches
+    t = timed(direct)
+    plan = h.batched_plan(items)                          # the same launch captured as a CUDA graph
+    t_graph = timed(plan.launch)
+    plan.close()
     ranks = R.cpu().numpy()
     wsum = sum(work_bits(sp["m"], sp["n"], int(rk)) for sp, rk in zip(specs, ranks))
     nbytes = 2 * 8 * tot
@@ -253,7 +271,12 @@ def bench_batched(h, torch, dev, stream, reps: int = 5):
             "ms": t, "mats_per_s": len(specs) / (t / 1e3), "gbitops": wsum / (t / 1e3) / 1e9,
             "hbm_gbs_algorithmic": nbytes / (t / 1e3) / 1e9,
             "hbm_frac": nbytes / (t / 1e3) / 1e9 / hbm,
-            "plain_ms": t_plain, "speedup_vs_plain": t_plain / t, "launches": 1}
+            "plain_ms": t_plain, "speedup_vs_plain": t_plain / t, "launches": 1,
+            "graph_replay_ms": t_graph, "default_config_ms": t_default,
+            "autotune": {"classes": "max(m,n) <= 128, 256, 512, 1024, 2048, 4096",
+                         "configs": "0: k=8 x8 tables, 2-word tiles; 1: k=8, 1 word; 2: k=4 x16, 1 word; "
+                                    "3: k=4, 2 words; 4: k=4, 4 words",
+                         "chosen": chosen, "ms_per_class_and_config": tune_ms}}
 
 
 def bench_served(h, torch, dev, rates=(200, 1000, 5000), jobs_per_rate=400, pool_size=48, slots=6):
@@ -320,6 +343,72 @@ def bench_served(h, torch, dev, rates=(200, 1000, 5000), jobs_per_rate=400, pool
     return out
 
 
+def tc_compare(args):
+    """Tensor-core (tcgen05) versus table forms of the product and of the PLE
+    trailing update, same inputs, CUDA-event medians; prints one JSON line."""
+    import torch
+    import gf2inputs as gi
+    import paper_1111_6549_gb300 as g
+    dev = torch.device("cuda", 0)
+    h = g.Handle(0)
+    stream = torch.cuda.current_stream(dev)
+
+    def timeit(fn, reps=5, pre=None):
+        ts = []
+        for i in range(reps + 2):
+            if pre:
+                pre()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    out = {"mode": "tc_compare", "mul": [], "ple": []}
+    for (m, k, n) in [(16384, 64, 16384), (16384, 1024, 16384), (16384, 16384, 16384)]:
+        A = torch.from_numpy(gi.bernoulli_matrix(m, k, 1).view(np.int64)).to(dev)
+        B = torch.from_numpy(gi.bernoulli_matrix(k, n, 2).view(np.int64)).to(dev)
+        C = torch.zeros((m, gi.words_for(n)), dtype=torch.int64, device=dev)
+        res, outs = {"m": m, "k": k, "n": n}, {}
+        for tc in (0, 1):
+            h.set_option(g.OPT_TC_MUL, tc)
+            res["tc_ms" if tc else "table_ms"] = timeit(lambda: h.mul(C, A, B, m, k, n))
+            outs[tc] = C.clone()
+        res["identical"] = bool(torch.equal(outs[0], outs[1]))
+        res["tc_tera_and_xor_per_s"] = m * k * n / (res["tc_ms"] / 1e3) / 1e12
+        res["table_tera_and_xor_per_s"] = m * k * n / (res["table_ms"] / 1e3) / 1e12
+        out["mul"].append(res)
+    h.set_option(g.OPT_TC_MUL, 0)
+    for nn in (16384, 32768):
+        A = torch.from_numpy(gi.dense_square(nn).view(np.int64)).to(dev)
+        Wk = torch.empty_like(A)
+        P = torch.empty(nn, dtype=torch.int64, device=dev)
+        Q = torch.empty_like(P)
+        R = torch.zeros(1, dtype=torch.int64, device=dev)
+        res, outs = {"n": nn}, {}
+        for tc in (0, 1):
+            h.set_option(g.OPT_TC_UPDATE, tc)
+            key = "tc" if tc else "table"
+            res[key + "_ms"] = timeit(lambda: h.ple_async(Wk, nn, nn, P, Q, R), reps=3, pre=lambda: Wk.copy_(A))
+            outs[tc] = Wk.clone()
+            h.reset_stats()
+            h.set_profiling(1)
+            Wk.copy_(A)
+            h.ple_async(Wk, nn, nn, P, Q, R)
+            torch.cuda.synchronize()
+            res[key + "_update_ms"] = h.stats()["update_ms"]
+            h.set_profiling(0)
+        res["identical"] = bool(torch.equal(outs[0], outs[1]))
+        out["ple"].append(res)
+    h.set_option(g.OPT_TC_UPDATE, 0)
+    h.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import gf2inputs as gi
@@ -346,7 +435,6 @@ def run_ours(args):
         work.copy_(pristine)
         step()
     torch.cuda.synchronize()
-    r = int(rank_dev.cpu()[0])
 
     # ---- timed region (device time of exactly K steps)
     h.reset_stats()
@@ -370,6 +458,7 @@ def run_ours(args):
     st = h.stats()
     h.set_profiling(0)
     ms = sum(a.elapsed_time(b) for a, b in ev)
+    r = int(rank_dev.cpu()[0])
     # diagnostic pass (not part of the timed steps): every kernel timed
     h.reset_stats()
     h.set_profiling(2)
@@ -489,10 +578,12 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": f"rref_via_ple dense Bernoulli(1/2) {m}x{n} GF(2), 512 MiB packed",
+                "config": {"workload": f"rref_via_ple dense Bernoulli(1/2) {m}x{n} GF(2), "
+                                       f"{m * W * 8 / 2**20:.0f} MiB packed",
                            "m": m, "n": n, "rank": r, "stripe_columns": 64,
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "inputs (512 MiB) larger than L2; fresh copy restored before each step",
+                           "l2": f"inputs ({m * W * 8 / 2**20:.0f} MiB) larger than L2; fresh copy restored "
+                                 "before each step",
                            "seconds_per_step": max_ms / args.steps / 1e3,
                            "ple_only_ms": ple_ms, "side_32768": side},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "served": served,
@@ -515,9 +606,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--tc-compare", action="store_true",
+                    help="only compare the tensor-core and table forms (product, PLE update)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.tc_compare:
+        return tc_compare(args)
     return run_ours(args)
 
 

@@ -142,6 +142,56 @@ typedef struct gf2_desc {
 } gf2_desc;
 int gf2_ple_batched(gf2_handle_t handle, const gf2_desc *descs, int64_t count);
 
+/*
+ * Tuning of the batched kernel (Algorithms 5 and 6 leave the table width
+ * open: the paper takes k near log2 n and four tables, Section 3.2 and the
+ * appendix).  Matrices fall into size classes by max(m, n):
+ *   class 0: <= 128, 1: <= 256, 2: <= 512, 3: <= 1024, 4: <= 2048, 5: <= 4096.
+ * Each class runs one table configuration for its 64-column stripes:
+ *   config 0: 8 tables of k = 8 bits, tiles of 2 words (default)
+ *   config 1: 8 tables of k = 8 bits, tiles of 1 word
+ *   config 2: 16 tables of k = 4 bits, tiles of 1 word
+ *   config 3: 16 tables of k = 4 bits, tiles of 2 words
+ *   config 4: 16 tables of k = 4 bits, tiles of 4 words
+ * Results never depend on the configuration.
+ * gf2_batched_config: set class size_class (-1: every class) to config
+ *   (-1: the default).  GF2_EINVAL for an unknown class or config.
+ * gf2_batched_get_config: configs (host int[GF2_BATCH_CLASSES]) <- current.
+ * gf2_batched_autotune: for each class, times every configuration on one
+ *   wave of seeded random matrices of that class (reps timed runs after a
+ *   warm-up, 1 <= reps <= 100) on the handle's stream and keeps the fastest.
+ *   ms_out (host double[GF2_BATCH_CLASSES * GF2_BATCH_CONFIGS], may be NULL)
+ *   receives the best time of each (class, config).  Synchronous; allocates
+ *   and frees up to about 1 GiB of device memory while it runs.
+ */
+#define GF2_BATCH_CLASSES 6
+#define GF2_BATCH_CONFIGS 5
+int gf2_batched_config(gf2_handle_t handle, int size_class, int config);
+int gf2_batched_get_config(gf2_handle_t handle, int *configs);
+int gf2_batched_autotune(gf2_handle_t handle, int reps, double *ms_out);
+
+/*
+ * A batched PLE captured once as a CUDA graph and replayed: for callers that
+ * run the same batch layout again and again (the matrices' contents change,
+ * their addresses and shapes do not).  Every matrix must be at most 4096 x
+ * 4096 (larger ones, or count == 0, give GF2_EINVAL), so the graph holds
+ * exactly the persistent launch of gf2_ple_batched, with the handle's
+ * current batched configuration.
+ * gf2_batched_plan_create: copies the descriptors into device memory owned by
+ *   the plan and captures the launch; the device buffers named by descs must
+ *   stay valid for the plan's lifetime.  Synchronous.
+ * gf2_batched_plan_launch: replays the graph on stream (a cudaStream_t as
+ *   void*; NULL: the handle's stream).  Asynchronous.  Replays of one plan
+ *   must not overlap each other.
+ * gf2_batched_plan_destroy: waits for the device to finish all work, then
+ *   frees the plan.
+ */
+typedef struct gf2_batched_plan *gf2_batched_plan_t;
+int gf2_batched_plan_create(gf2_handle_t handle, const gf2_desc *descs, int64_t count,
+                            gf2_batched_plan_t *plan);
+int gf2_batched_plan_launch(gf2_batched_plan_t plan, void *stream);
+int gf2_batched_plan_destroy(gf2_batched_plan_t plan);
+
 /* Device workspace gf2_ple / gf2_rref need for an m x n matrix, in bytes. */
 size_t gf2_workspace_bytes(gf2_handle_t handle, int64_t m, int64_t n);
 
@@ -218,6 +268,21 @@ int gf2_server_drain(gf2_server_t server);
 double gf2_server_clock(void);
 /* Finish every queued job, then stop the worker and free everything. */
 int gf2_server_destroy(gf2_server_t server);
+
+/*
+ * Execution options of a handle (value 0 = off, 1 = on):
+ *   GF2_OPT_LOOKAHEAD  overlap each stripe's pivot search with the previous
+ *                      stripe's trailing update on a side stream (default on)
+ *   GF2_OPT_TC_MUL     gf2_mul on the tensor cores: 0/1 operands in FP8, the
+ *                      counts accumulated in tensor memory and reduced mod 2
+ *   GF2_OPT_TC_UPDATE  the PLE / RREF trailing updates on the tensor cores
+ *                      instead of the Four-Russians tables
+ * Results are identical either way; only the speed differs.
+ */
+#define GF2_OPT_LOOKAHEAD 1
+#define GF2_OPT_TC_MUL    2
+#define GF2_OPT_TC_UPDATE 3
+int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */
 typedef struct gf2_stats {

@@ -24,6 +24,8 @@ __all__ = ["Handle", "GF2Error", "load", "lib_path", "SOLVE_UNIQUE", "SOLVE_UNDE
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
+OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE = 1, 2, 3
+BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
 
 
@@ -100,6 +102,13 @@ def load():
             "gf2_reset_stats": ([vp], ctypes.c_int),
             "gf2_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "gf2_solve_async": ([vp, vp, i64, i64, vp, i64, i64, vp], ctypes.c_int),
+            "gf2_set_option": ([vp, ctypes.c_int, i64], ctypes.c_int),
+            "gf2_batched_config": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "gf2_batched_get_config": ([vp, i32p], ctypes.c_int),
+            "gf2_batched_autotune": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "gf2_batched_plan_create": ([vp, ctypes.POINTER(Desc), i64, ctypes.POINTER(vp)], ctypes.c_int),
+            "gf2_batched_plan_launch": ([vp, vp], ctypes.c_int),
+            "gf2_batched_plan_destroy": ([vp], ctypes.c_int),
             "gf2_server_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, i64, i64, ctypes.c_size_t],
                                   ctypes.c_int),
             "gf2_server_submit": ([vp, ctypes.POINTER(SolveJob)], ctypes.c_int),
@@ -229,12 +238,38 @@ class Handle:
 
     def ple_batched(self, items) -> None:
         """items: sequence of (A, m, n, P, Q, rank_dev) device tensors / sizes."""
+        arr = self._descs(items)
+        self._bind_stream()
+        _check(load().gf2_ple_batched(self._h, arr, len(items)), "gf2_ple_batched")
+
+    @staticmethod
+    def _descs(items):
         arr = (Desc * len(items))()
         for i, (A, m, n, P, Q, rk) in enumerate(items):
             ld = _mat(A, m, n)
             arr[i] = Desc(_dptr(A), m, n, ld, _dptr(P), _dptr(Q), _dptr(rk))
+        return arr
+
+    def batched_config(self, size_class: int, config: int) -> None:
+        """Table configuration of the batched kernel for a size class (-1: all)."""
+        _check(load().gf2_batched_config(self._h, size_class, config), "gf2_batched_config")
+
+    def batched_get_config(self) -> list:
+        out = (ctypes.c_int * BATCH_CLASSES)()
+        _check(load().gf2_batched_get_config(self._h, out), "gf2_batched_get_config")
+        return list(out)
+
+    def batched_autotune(self, reps: int = 3):
+        """Time every configuration per size class and keep the fastest;
+        returns (chosen configs, ms[class][config])."""
+        ms = (ctypes.c_double * (BATCH_CLASSES * BATCH_CONFIGS))()
         self._bind_stream()
-        _check(load().gf2_ple_batched(self._h, arr, len(items)), "gf2_ple_batched")
+        _check(load().gf2_batched_autotune(self._h, reps, ms), "gf2_batched_autotune")
+        table = [[ms[c * BATCH_CONFIGS + k] for k in range(BATCH_CONFIGS)] for c in range(BATCH_CLASSES)]
+        return self.batched_get_config(), table
+
+    def batched_plan(self, items) -> "BatchedPlan":
+        return BatchedPlan(self, items)
 
     def solve_async(self, A, B, n: int, nrhs: int, status_dev) -> None:
         lda = _mat(A, n, n)
@@ -273,6 +308,10 @@ class Handle:
         _check(load().gf2_rref_host(self._h, aptr, m, n, ld, qptr, ctypes.byref(rank)), "gf2_rref_host")
         return rank.value
 
+    def set_option(self, option: int, value: int) -> None:
+        """OPT_LOOKAHEAD / OPT_TC_MUL / OPT_TC_UPDATE (0 off, 1 on); results are identical."""
+        _check(load().gf2_set_option(self._h, option, int(value)), "gf2_set_option")
+
     # ---- statistics -----------------------------------------------------
     def set_profiling(self, level) -> None:
         """0: off, 1 (or True): time the update kernel, 2: time every kernel."""
@@ -285,6 +324,34 @@ class Handle:
 
     def reset_stats(self) -> None:
         _check(load().gf2_reset_stats(self._h), "gf2_reset_stats")
+
+
+class BatchedPlan:
+    """gf2_batched_plan_*: one batch layout captured as a CUDA graph; launch()
+    replays it on the current torch stream."""
+
+    def __init__(self, handle: Handle, items):
+        self._handle = handle
+        self._p = ctypes.c_void_p()
+        arr = Handle._descs(items)
+        _check(load().gf2_batched_plan_create(handle._h, arr, len(items), ctypes.byref(self._p)),
+               "gf2_batched_plan_create")
+
+    def launch(self) -> None:
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+        _check(load().gf2_batched_plan_launch(self._p, ctypes.c_void_p(st)), "gf2_batched_plan_launch")
+
+    def close(self) -> None:
+        if self._p:
+            load().gf2_batched_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _default = {}

@@ -25,6 +25,8 @@ struct gf2_handle {
     cudaStream_t side = nullptr;   // look-ahead panels run here, overlapping the update
     cudaEvent_t ev_fork = nullptr, ev_u1 = nullptr, ev_p = nullptr;
     bool lookahead = true;
+    bool tc_mul = false;           // products on the tensor cores
+    bool tc_update = false;        // PLE / RREF trailing updates on the tensor cores
     int num_sms = 1;
     char *ws = nullptr;        // stripe records, indices, staged rows, panel scratch
     size_t ws_cap = 0;
@@ -40,6 +42,7 @@ struct gf2_handle {
     struct Pending { cudaEvent_t e0, e1; int kind; };
     std::vector<Pending> ev_pending;
     double kind_ms[5] = {0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other
+    BatchTune btune{};             // batched kernel: table configuration per size class
 };
 
 namespace {
@@ -166,10 +169,14 @@ struct Timed {
     }
 };
 
-int launch_update_counted(gf2_handle *h, const UpdArgs &a)
+int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
 {
     Timed t(h, K_UPDATE);
-    CK(launch_update(h->stream, a, h->num_sms));
+    UpdArgs a = a_in;
+    a.err = err_dev(h);
+    const bool tc = (a.mode == UPD_MUL) ? h->tc_mul : h->tc_update;
+    if (tc) CK(launch_update_tc(h->stream, a, h->num_sms));
+    else CK(launch_update(h->stream, a, h->num_sms));
     h->launches += 1;
     h->upd_launches += 1;
     return GF2_OK;
@@ -243,7 +250,8 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     probe.ld = ld;
     probe.S = S;
     probe.ldS = L.ldS;
-    const bool la = h->lookahead && h->side && ns > 1 && update_vectorised(probe) && h->num_sms >= 8;
+    const bool la = h->lookahead && !h->tc_update && h->side && ns > 1 && update_vectorised(probe) &&
+                    h->num_sms >= 8;
     if (!la) {
         for (int64_t s = 0; s < ns; ++s) {
             if ((rc = panel(h->stream, s))) return rc;
@@ -336,7 +344,7 @@ int finish_sync(gf2_handle *h)
     if (err) {
         int32_t zero = 0;
         cudaMemcpy(err_dev(h), &zero, sizeof(zero), cudaMemcpyHostToDevice);
-        return GF2_EINTERNAL;
+        return err == GF2_ETIMEOUT ? GF2_ETIMEOUT : GF2_EINTERNAL;
     }
     return GF2_OK;
 }
@@ -369,6 +377,7 @@ int gf2_create(gf2_handle_t *handle, int device)
     gf2_handle *h = new (std::nothrow) gf2_handle();
     if (!h) return GF2_ENOMEM;
     h->device = dev;
+    for (int c = 0; c < BATCH_CLASSES; ++c) h->btune.cfg[c] = BATCH_CFG_DEFAULT;
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete h;
         return GF2_ECUDA;
@@ -519,6 +528,35 @@ int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t
     const int64_t Wc = words_for(n);
     if (!accumulate)
         CK(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)Wc * 8, (size_t)m, h->stream));
+    if (h->tc_mul && k > 0) {
+        // tensor cores: every 64-column chunk of A accumulates into the same
+        // counts in tensor memory, so C is read and written once per group of
+        // up to 2^22 columns of A (fp32 counts stay exact below 2^24)
+        constexpr int64_t KG = int64_t(1) << 22;
+        for (int64_t k0 = 0; k0 < k; k0 += KG) {
+            UpdArgs a{};
+            a.tp_lo = 0;
+            a.tp_hi = -1;
+            a.left_copies = 1;
+            a.mode = UPD_MUL;
+            a.A = C;
+            a.ld = ldc;
+            a.m = m;
+            a.W = Wc;
+            a.idx = A + k0 / 64;
+            a.idx_stride = lda;
+            a.B = B + k0 * ldb;
+            a.ldb = ldb;
+            a.gen_count = std::min(KG, k - k0);
+            a.row_lo = 0;
+            a.row_hi = m;
+            a.w_lo = 0;
+            a.bytes = bytes_dev(h);
+            const int rc = launch_update_counted(h, a);
+            if (rc) return rc;
+        }
+        return GF2_OK;
+    }
     for (int64_t kc = 0; kc < words_for(k); ++kc) {
         UpdArgs a{};
         a.tp_lo = 0;
@@ -624,7 +662,57 @@ int gf2_solve(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, 
 
 static_assert(sizeof(gf2_desc) == sizeof(gf2_batch_item), "gf2_desc and gf2_batch_item must match");
 
-int gf2_ple_batched(gf2_handle_t h, const gf2_desc *descs, int64_t count)
+namespace {
+
+// Matrices up to BATCH_MAX_ROWS x BATCH_MAX_COLS go to the persistent batched
+// kernel, largest first; bigger ones take the single-matrix path.
+struct BatchSplit {
+    std::vector<int32_t> small;
+    std::vector<int64_t> large;
+    int64_t max_rows = 1, max_w = 1;
+};
+
+BatchSplit split_batch(const gf2_desc *descs, int64_t count)
+{
+    BatchSplit b;
+    for (int64_t i = 0; i < count; ++i) {
+        const gf2_desc &d = descs[i];
+        if (d.m <= BATCH_MAX_ROWS && d.n <= BATCH_MAX_COLS) {
+            b.small.push_back((int32_t)i);
+            b.max_rows = std::max(b.max_rows, d.m);
+            b.max_w = std::max(b.max_w, words_for(d.n));
+        } else {
+            b.large.push_back(i);
+        }
+    }
+    std::stable_sort(b.small.begin(), b.small.end(), [&](int32_t x, int32_t y) {
+        return descs[x].m * descs[x].n > descs[y].m * descs[y].n;
+    });
+    return b;
+}
+
+// Device buffer of one batched launch: descriptors, order, work counter,
+// per-CTA scratch.
+struct BatchBuf {
+    size_t items, order, next, scratch, total;
+    int64_t ldS;
+    int grid;
+};
+
+BatchBuf batch_buf(int num_sms, int64_t count, const BatchSplit &b)
+{
+    BatchBuf L{};
+    L.ldS = b.max_w + (b.max_w & 1);
+    L.grid = (int)std::min<int64_t>(batched_grid(num_sms), (int64_t)std::max<size_t>(b.small.size(), 1));
+    L.items = 0;
+    L.order = align256((size_t)count * sizeof(gf2_desc));
+    L.next = L.order + align256(std::max<size_t>(b.small.size(), 1) * sizeof(int32_t));
+    L.scratch = L.next + 256;
+    L.total = L.scratch + align256(batched_scratch_words(b.max_rows, L.ldS, L.grid) * 8);
+    return L;
+}
+
+int check_batch(gf2_handle *h, const gf2_desc *descs, int64_t count)
 {
     if (!h || count < 0 || (count > 0 && !descs)) return GF2_EINVAL;
     if (count > INT32_MAX / 2) return GF2_EINVAL;
@@ -634,50 +722,253 @@ int gf2_ple_batched(gf2_handle_t h, const gf2_desc *descs, int64_t count)
         if (rc) return rc;
         if (!d.rank || (d.m > 0 && !d.P) || (d.m > 0 && d.n > 0 && !d.Q)) return GF2_EINVAL;
     }
+    return GF2_OK;
+}
+
+// Enqueue the persistent kernel over the small matrices of a batch whose
+// descriptors and order already sit in buf.
+int enqueue_batched(gf2_handle *h, cudaStream_t st, char *buf, const BatchBuf &L, const BatchSplit &b,
+                    const BatchTune &tune)
+{
+    auto *items = reinterpret_cast<gf2_batch_item *>(buf + L.items);
+    auto *order = reinterpret_cast<int32_t *>(buf + L.order);
+    auto *next = reinterpret_cast<int32_t *>(buf + L.next);
+    auto *scratch = reinterpret_cast<uint64_t *>(buf + L.scratch);
+    CK(cudaMemsetAsync(next, 0, sizeof(int32_t), st));
+    CK(launch_batched(st, items, order, (int)b.small.size(), next, scratch, b.max_rows, L.ldS, L.grid, tune));
+    h->launches += 1;
+    return GF2_OK;
+}
+
+}  // namespace
+
+int gf2_ple_batched(gf2_handle_t h, const gf2_desc *descs, int64_t count)
+{
+    int rc = check_batch(h, descs, count);
+    if (rc) return rc;
     DeviceGuard g(h->device);
-    // Matrices up to BATCH_MAX_ROWS x BATCH_MAX_COLS go to the persistent
-    // batched kernel, largest first; bigger ones take the single-matrix path.
-    std::vector<int32_t> small;
-    std::vector<int64_t> large;
-    int64_t max_rows = 1, max_w = 1;
-    for (int64_t b = 0; b < count; ++b) {
-        const gf2_desc &d = descs[b];
-        if (d.m <= BATCH_MAX_ROWS && d.n <= BATCH_MAX_COLS) {
-            small.push_back((int32_t)b);
-            max_rows = std::max(max_rows, d.m);
-            max_w = std::max(max_w, words_for(d.n));
-        } else {
-            large.push_back(b);
-        }
-    }
-    if (!small.empty()) {
-        std::stable_sort(small.begin(), small.end(), [&](int32_t x, int32_t y) {
-            return descs[x].m * descs[x].n > descs[y].m * descs[y].n;
-        });
-        const int64_t ldS = max_w + (max_w & 1);
-        const int grid = (int)std::min<int64_t>(batched_grid(h->num_sms), (int64_t)small.size());
-        const size_t items_bytes = align256((size_t)count * sizeof(gf2_desc));
-        const size_t order_bytes = align256(small.size() * sizeof(int32_t));
-        const size_t next_bytes = 256;
-        const size_t scratch_bytes = align256(batched_scratch_words(max_rows, ldS, grid) * 8);
-        int rc = grow(&h->bws, &h->bws_cap, items_bytes + order_bytes + next_bytes + scratch_bytes, h->stream);
+    const BatchSplit b = split_batch(descs, count);
+    if (!b.small.empty()) {
+        const BatchBuf L = batch_buf(h->num_sms, count, b);
+        rc = grow(&h->bws, &h->bws_cap, L.total, h->stream);
         if (rc) return rc;
-        auto *items = reinterpret_cast<gf2_batch_item *>(h->bws);
-        auto *order = reinterpret_cast<int32_t *>(h->bws + items_bytes);
-        auto *next = reinterpret_cast<int32_t *>(h->bws + items_bytes + order_bytes);
-        auto *scratch = reinterpret_cast<uint64_t *>(h->bws + items_bytes + order_bytes + next_bytes);
-        CK(cudaMemcpyAsync(items, descs, (size_t)count * sizeof(gf2_desc), cudaMemcpyHostToDevice, h->stream));
-        CK(cudaMemcpyAsync(order, small.data(), small.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+        CK(cudaMemcpyAsync(h->bws + L.items, descs, (size_t)count * sizeof(gf2_desc), cudaMemcpyHostToDevice,
                            h->stream));
-        CK(cudaMemsetAsync(next, 0, sizeof(int32_t), h->stream));
-        CK(launch_batched(h->stream, items, order, (int)small.size(), next, scratch, max_rows, ldS, grid));
-        h->launches += 1;
-    }
-    for (int64_t b : large) {
-        const gf2_desc &d = descs[b];
-        int rc = gf2_ple_async(h, d.A, d.m, d.n, d.ld_words, d.P, d.Q, d.rank);
+        CK(cudaMemcpyAsync(h->bws + L.order, b.small.data(), b.small.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, h->stream));
+        rc = enqueue_batched(h, h->stream, h->bws, L, b, h->btune);
         if (rc) return rc;
     }
+    for (int64_t i : b.large) {
+        const gf2_desc &d = descs[i];
+        rc = gf2_ple_async(h, d.A, d.m, d.n, d.ld_words, d.P, d.Q, d.rank);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+static_assert(GF2_BATCH_CLASSES == BATCH_CLASSES && GF2_BATCH_CONFIGS == BATCH_CONFIGS, "batched tuning sizes");
+
+int gf2_batched_config(gf2_handle_t h, int size_class, int config)
+{
+    if (!h || size_class < -1 || size_class >= BATCH_CLASSES || config < -1 || config >= BATCH_CONFIGS)
+        return GF2_EINVAL;
+    const int8_t v = (int8_t)(config < 0 ? BATCH_CFG_DEFAULT : config);
+    if (size_class < 0)
+        for (int c = 0; c < BATCH_CLASSES; ++c) h->btune.cfg[c] = v;
+    else
+        h->btune.cfg[size_class] = v;
+    return GF2_OK;
+}
+
+int gf2_batched_get_config(gf2_handle_t h, int *configs)
+{
+    if (!h || !configs) return GF2_EINVAL;
+    for (int c = 0; c < BATCH_CLASSES; ++c) configs[c] = h->btune.cfg[c];
+    return GF2_OK;
+}
+
+int gf2_batched_autotune(gf2_handle_t h, int reps, double *ms_out)
+{
+    if (!h || reps < 1 || reps > 100) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    int rc = finish_sync(h);
+    if (rc) return rc;
+    const int grid = batched_grid(h->num_sms);
+    uint64_t state = 0x243F6A8885A308D3ull;
+    auto next_u = [&](int64_t lo, int64_t hi) {      // splitmix64, uniform in [lo, hi]
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return lo + (int64_t)(z % (uint64_t)(hi - lo + 1));
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return GF2_ECUDA;
+    }
+    for (int c = 0; c < BATCH_CLASSES && !rc; ++c) {
+        // one wave of matrices of this class, at most 512 MiB of them
+        const int64_t hi = int64_t(128) << c, lo = (c == 0) ? 64 : hi / 2 + 1;
+        std::vector<gf2_desc> descs;
+        size_t words = 0;
+        while ((int)descs.size() < grid && words * 8 < (size_t(512) << 20)) {
+            gf2_desc d{};
+            d.m = next_u(lo, hi);
+            d.n = next_u(lo, hi);
+            d.ld_words = words_for(d.n);
+            d.A = reinterpret_cast<uint64_t *>(words);          // offset for now
+            words += (size_t)d.m * d.ld_words;
+            descs.push_back(d);
+        }
+        const int64_t count = (int64_t)descs.size();
+        const size_t abytes = align256(words * 8);
+        const size_t pbytes = align256((size_t)count * (size_t)hi * 8);
+        char *tbuf = nullptr;
+        if (cudaMalloc(reinterpret_cast<void **>(&tbuf), 2 * abytes + 2 * pbytes + align256((size_t)count * 8)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            rc = GF2_ENOMEM;
+            break;
+        }
+        uint64_t *work = reinterpret_cast<uint64_t *>(tbuf), *pristine = reinterpret_cast<uint64_t *>(tbuf + abytes);
+        int64_t *P = reinterpret_cast<int64_t *>(tbuf + 2 * abytes);
+        int64_t *Q = reinterpret_cast<int64_t *>(tbuf + 2 * abytes + pbytes);
+        int64_t *R = reinterpret_cast<int64_t *>(tbuf + 2 * abytes + 2 * pbytes);
+        std::vector<gf2_desc> fill = descs;
+        for (int64_t i = 0; i < count; ++i) {
+            const size_t off = reinterpret_cast<size_t>(descs[i].A);
+            descs[i].A = work + off;
+            fill[i].A = pristine + off;
+            descs[i].P = fill[i].P = P + i * hi;
+            descs[i].Q = fill[i].Q = Q + i * hi;
+            descs[i].rank = fill[i].rank = R + i;
+        }
+        const BatchSplit b = split_batch(descs.data(), count);
+        const BatchBuf L = batch_buf(h->num_sms, count, b);
+        rc = grow(&h->bws, &h->bws_cap, L.total, h->stream);
+        if (!rc && (cudaMemcpyAsync(h->bws + L.items, fill.data(), (size_t)count * sizeof(gf2_desc),
+                                    cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+                    launch_batch_fill(h->stream, reinterpret_cast<gf2_batch_item *>(h->bws + L.items), (int)count,
+                                      0x9E3779B97F4A7C15ull * (c + 1), h->num_sms) != cudaSuccess ||
+                    cudaMemcpyAsync(h->bws + L.items, descs.data(), (size_t)count * sizeof(gf2_desc),
+                                    cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(h->bws + L.order, b.small.data(), b.small.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, h->stream) != cudaSuccess)) {
+            cudaGetLastError();
+            rc = GF2_ECUDA;
+        }
+        double best = 1e30;
+        int best_cfg = BATCH_CFG_DEFAULT;
+        for (int cfg = 0; cfg < BATCH_CONFIGS && !rc; ++cfg) {
+            BatchTune t = h->btune;
+            t.cfg[c] = (int8_t)cfg;
+            double tmin = 1e30;
+            for (int k = 0; k <= reps && !rc; ++k) {      // the first run is a warm-up
+                float ms = 0.f;
+                if (cudaMemcpyAsync(work, pristine, words * 8, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+                    cudaEventRecord(e0, h->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = GF2_ECUDA;
+                    break;
+                }
+                rc = enqueue_batched(h, h->stream, h->bws, L, b, t);
+                if (rc) break;
+                if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = GF2_ECUDA;
+                    break;
+                }
+                if (k > 0) tmin = std::min(tmin, (double)ms);
+            }
+            if (ms_out) ms_out[c * BATCH_CONFIGS + cfg] = tmin;
+            if (tmin < best) { best = tmin; best_cfg = cfg; }
+        }
+        if (!rc) h->btune.cfg[c] = (int8_t)best_cfg;
+        cudaStreamSynchronize(h->stream);
+        cudaFree(tbuf);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = finish_sync(h);
+    return rc;
+}
+
+struct gf2_batched_plan {
+    gf2_handle *h = nullptr;
+    char *buf = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int gf2_batched_plan_create(gf2_handle_t h, const gf2_desc *descs, int64_t count, gf2_batched_plan_t *plan)
+{
+    if (!plan) return GF2_EINVAL;
+    *plan = nullptr;
+    int rc = check_batch(h, descs, count);
+    if (rc) return rc;
+    if (count == 0) return GF2_EINVAL;
+    const BatchSplit b = split_batch(descs, count);
+    if (!b.large.empty()) return GF2_EINVAL;       // plans hold only the persistent launch
+    DeviceGuard g(h->device);
+    gf2_batched_plan *p = new (std::nothrow) gf2_batched_plan();
+    if (!p) return GF2_ENOMEM;
+    p->h = h;
+    const BatchBuf L = batch_buf(h->num_sms, count, b);
+    auto fail = [&](int code) {
+        cudaGetLastError();
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        if (p->cap) cudaStreamDestroy(p->cap);
+        cudaFree(p->buf);
+        delete p;
+        return code;
+    };
+    if (cudaMalloc(reinterpret_cast<void **>(&p->buf), L.total) != cudaSuccess) return fail(GF2_ENOMEM);
+    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(GF2_ECUDA);
+    if (cudaMemcpyAsync(p->buf + L.items, descs, (size_t)count * sizeof(gf2_desc), cudaMemcpyHostToDevice,
+                        p->cap) != cudaSuccess ||
+        cudaMemcpyAsync(p->buf + L.order, b.small.data(), b.small.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        p->cap) != cudaSuccess ||
+        cudaStreamSynchronize(p->cap) != cudaSuccess)
+        return fail(GF2_ECUDA);
+    if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(GF2_ECUDA);
+    const int64_t launches = h->launches;
+    rc = enqueue_batched(h, p->cap, p->buf, L, b, h->btune);
+    h->launches = launches;                         // counted when the graph runs
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->cap, &graph);
+    p->graph = graph;
+    if (rc || ec != cudaSuccess) return fail(rc ? rc : GF2_ECUDA);
+    if (cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) return fail(GF2_ECUDA);
+    *plan = p;
+    return GF2_OK;
+}
+
+int gf2_batched_plan_launch(gf2_batched_plan_t p, void *stream)
+{
+    if (!p) return GF2_EINVAL;
+    DeviceGuard g(p->h->device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : p->h->stream;
+    CK(cudaGraphLaunch(p->exec, st));
+    p->h->launches += 1;
+    return GF2_OK;
+}
+
+int gf2_batched_plan_destroy(gf2_batched_plan_t p)
+{
+    if (!p) return GF2_EINVAL;
+    DeviceGuard g(p->h->device);
+    cudaDeviceSynchronize();                        // no replay may still use the buffer
+    cudaGraphExecDestroy(p->exec);
+    cudaGraphDestroy(p->graph);
+    cudaStreamDestroy(p->cap);
+    cudaFree(p->buf);
+    delete p;
     return GF2_OK;
 }
 
@@ -735,6 +1026,17 @@ int gf2_rref_host(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld,
     CK(cudaMemcpyAsync(Q, dQ, (size_t)qn * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(rank, r_dev(h), 8, cudaMemcpyDeviceToHost, h->stream));
     return finish_sync(h);
+}
+
+int gf2_set_option(gf2_handle_t h, int option, int64_t value)
+{
+    if (!h) return GF2_EINVAL;
+    switch (option) {
+    case GF2_OPT_LOOKAHEAD: h->lookahead = value != 0; return GF2_OK;
+    case GF2_OPT_TC_MUL: h->tc_mul = value != 0; return GF2_OK;
+    case GF2_OPT_TC_UPDATE: h->tc_update = value != 0; return GF2_OK;
+    default: return GF2_EINVAL;
+    }
 }
 
 int gf2_set_profiling(gf2_handle_t h, int on)

@@ -52,6 +52,24 @@ struct gf2_batch_item {
 constexpr int64_t BATCH_MAX_ROWS = 4096;   // larger matrices take the single-matrix path
 constexpr int64_t BATCH_MAX_COLS = 4096;
 
+// Tuning of the batched kernel.  A matrix's size class is set by max(m, n):
+// <= 128, <= 256, <= 512, <= 1024, <= 2048, <= 4096.  Each class runs one
+// table configuration: k-bit tables (64 / k of them per stripe) over tiles of
+// BW words.
+constexpr int BATCH_CLASSES = 6;
+constexpr int BATCH_CONFIGS = 5;
+constexpr int BATCH_CFG_K[BATCH_CONFIGS] = {8, 8, 4, 4, 4};
+constexpr int BATCH_CFG_BW[BATCH_CONFIGS] = {2, 1, 1, 2, 4};
+constexpr int BATCH_CFG_DEFAULT = 0;
+struct BatchTune {
+    int8_t cfg[BATCH_CLASSES];
+};
+__host__ __device__ inline int batch_size_class(int64_t m, int64_t n)
+{
+    const int64_t s = m > n ? m : n;
+    return s <= 128 ? 0 : s <= 256 ? 1 : s <= 512 ? 2 : s <= 1024 ? 3 : s <= 2048 ? 4 : 5;
+}
+
 // Scratch of the block-wide panel path: one entry per remaining row.
 struct PanelScratch {
     uint64_t *val;   // stripe word, eliminated eagerly
@@ -83,6 +101,7 @@ struct UpdArgs {
     int64_t tp_lo, tp_hi;      // tile pairs [tp_lo, tp_hi) of the column range (tp_hi < 0: all)
     int left_copies;           // PLE: also write the staged rows' left parts
     int grid;                  // CTAs to launch (0: one per SM)
+    int32_t *err;              // device error word (bounded waits that expire), may be null
 };
 
 // ---- launchers (host side, defined in the .cu files) ----
@@ -97,6 +116,7 @@ cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int
 cudaError_t setup_update_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
 bool update_vectorised(const UpdArgs &a);   // true when the paired, pipelined form runs
+cudaError_t launch_update_tc(cudaStream_t st, const UpdArgs &a, int num_sms);
 cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t W, int64_t ld,
                                const int64_t *r_dev, int num_sms);
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
@@ -105,7 +125,10 @@ cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *ran
 cudaError_t launch_solve_status(cudaStream_t st, const int64_t *r_dev, const int32_t *flag, int64_t n,
                                 int32_t *status);
 cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const int32_t *order, int count,
-                           int32_t *next, uint64_t *scratch, int64_t max_rows, int64_t ldS, int grid);
+                           int32_t *next, uint64_t *scratch, int64_t max_rows, int64_t ldS, int grid,
+                           BatchTune tune);
+cudaError_t launch_batch_fill(cudaStream_t st, const gf2_batch_item *items, int count, uint64_t seed,
+                              int num_sms);
 size_t batched_scratch_words(int64_t max_rows, int64_t ldS, int grid);
 size_t batched_smem_bytes();
 int batched_grid(int num_sms);

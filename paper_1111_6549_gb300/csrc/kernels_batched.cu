@@ -15,8 +15,13 @@
 namespace gf2 {
 
 constexpr int BATCH_THREADS = 256;
-constexpr int BTW = 2;                               // table tile: 2 words (16 bytes) per row
-constexpr int BTAB_WORDS = NTAB * 256 * BTW;         // 32 KiB of tables
+constexpr int BTAB_WORDS = 4096;                     // 32 KiB of tables: the largest configuration
+constexpr int BG_WORDS = KS * 4;                     // generator words of a tile: 64 rows x up to 4 words
+
+constexpr int cfg_table_words(int k, int bw) { return (KS / k) * (1 << k) * bw; }
+static_assert(cfg_table_words(8, 2) <= BTAB_WORDS && cfg_table_words(8, 1) <= BTAB_WORDS &&
+              cfg_table_words(4, 1) <= BTAB_WORDS && cfg_table_words(4, 2) <= BTAB_WORDS &&
+              cfg_table_words(4, 4) <= BTAB_WORDS, "table configuration larger than the table buffer");
 
 struct BatchScratch {
     uint64_t *idx;       // per CTA: max_rows words
@@ -42,16 +47,87 @@ __device__ __forceinline__ void batch_write_lregion(uint64_t *row, int64_t r, in
     if (cw > wl) row[cw] = es;
 }
 
+// The tabulated update (Algorithms 5 and 6) of the words [w_lo, W) of every
+// row at a position >= r, one tile of BW words at a time: the 64 / K tables of
+// a tile hold, for every K-bit value e, the XOR of the generator rows selected
+// by e (generators K tau .. K tau + K - 1 for table tau), and each row XORs in
+// one entry per table, chosen by the matching K bits of its index word.
+template <int K, int BW>
+__device__ __forceinline__ void batch_tables_update(uint64_t *T, uint64_t *sG, const uint64_t *S, int64_t ldS,
+                                                    uint64_t *A, int64_t ld, int64_t r, int64_t rows, int64_t W,
+                                                    int64_t w_lo, int rbar, const int16_t *smap, int maxpos,
+                                                    const uint64_t *idx)
+{
+    constexpr int NT = KS / K, NE = 1 << K;
+    const int tid = threadIdx.x;
+    for (int64_t wbase = (w_lo / BW) * BW; wbase < W; wbase += BW) {
+        for (int t = tid; t < KS * BW; t += BATCH_THREADS) {
+            const int g = t / BW, x = t - g * BW;
+            sG[t] = (g < rbar && wbase + x < W) ? S[(int64_t)g * ldS + wbase + x] : 0ull;
+        }
+        __syncthreads();
+        for (int e2 = tid; e2 < NT * NE; e2 += BATCH_THREADS) {
+            const int tau = e2 >> K, e = e2 & (NE - 1);
+            uint64_t acc[BW];
+#pragma unroll
+            for (int x = 0; x < BW; ++x) acc[x] = 0;
+#pragma unroll
+            for (int bq = 0; bq < K; ++bq) {
+                const uint64_t msk = 0ull - (uint64_t)((e >> bq) & 1);
+#pragma unroll
+                for (int x = 0; x < BW; ++x) acc[x] ^= sG[(K * tau + bq) * BW + x] & msk;
+            }
+#pragma unroll
+            for (int x = 0; x < BW; ++x) T[(size_t)e2 * BW + x] = acc[x];
+        }
+        __syncthreads();
+        for (int64_t off = tid; off < rows; off += BATCH_THREADS) {
+            const int k = (off <= maxpos) ? smap[off] : -1;
+            const uint64_t *src = (k >= 0) ? S + (int64_t)k * ldS : A + (r + off) * ld;
+            uint64_t *dst = A + (r + off) * ld;
+            const uint64_t ix = idx[off];
+            uint64_t acc[BW];
+#pragma unroll
+            for (int x = 0; x < BW; ++x) {
+                const int64_t w = wbase + x;
+                acc[x] = (w >= w_lo && w < W) ? src[w] : 0ull;
+            }
+#pragma unroll
+            for (int tau = 0; tau < NT; ++tau) {
+                const int e = (int)((ix >> (K * tau)) & (uint64_t)(NE - 1));
+                const uint64_t *te = T + ((size_t)tau * NE + e) * BW;
+                if constexpr (BW % 2 == 0) {
+#pragma unroll
+                    for (int x = 0; x < BW; x += 2) {
+                        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(te + x);
+                        acc[x] ^= v.x;
+                        acc[x + 1] ^= v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int x = 0; x < BW; ++x) acc[x] ^= te[x];
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < BW; ++x) {
+                const int64_t w = wbase + x;
+                if (w >= w_lo && w < W) dst[w] = acc[x];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(BATCH_THREADS, 4)
 batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count, int32_t *next,
-                   BatchScratch scr)
+                   BatchScratch scr, uint32_t tune_bits)
 {
-    extern __shared__ __align__(16) uint64_t T[];    // BTAB_WORDS: [table][entry][BTW]
+    extern __shared__ __align__(16) uint64_t T[];    // BTAB_WORDS: [table][entry][tile word]
     __shared__ PanelShared sh;
     __shared__ uint64_t sLinv[KS];
     __shared__ int16_t smap[BATCH_MAX_ROWS];          // position offset -> staged slot, or -1
     __shared__ int sh_item;
-    __shared__ uint64_t sG[KS * BTW];                 // generator words of the current tile
+    __shared__ __align__(16) uint64_t sG[BG_WORDS];   // generator words of the current tile
 
     const int tid = threadIdx.x, warp = tid >> 5;
     uint64_t *idx = scr.idx + (size_t)blockIdx.x * scr.max_rows;
@@ -126,55 +202,14 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
                 idx[off] = ix;
             }
             __syncthreads();
-            // tabulated update of the words right of the stripe
-            const int64_t w_lo = cw + 1;
-            for (int64_t wbase = (w_lo / BTW) * BTW; wbase < W; wbase += BTW) {
-                // T[tau][e][x] = XOR of generator rows 8 tau + bit of e, word wbase + x
-                for (int t = tid; t < KS * BTW; t += BATCH_THREADS) {
-                    const int g = t / BTW, x = t - g * BTW;
-                    sG[t] = (g < rbar && wbase + x < W) ? S[(int64_t)g * ldS + wbase + x] : 0ull;
-                }
-                __syncthreads();
-                for (int e2 = tid; e2 < NTAB * 256; e2 += BATCH_THREADS) {
-                    const int tau = e2 >> 8, e = e2 & 255;
-                    uint64_t acc[BTW];
-#pragma unroll
-                    for (int x = 0; x < BTW; ++x) acc[x] = 0;
-#pragma unroll
-                    for (int bq = 0; bq < 8; ++bq) {
-                        const uint64_t msk = 0ull - (uint64_t)((e >> bq) & 1);
-#pragma unroll
-                        for (int x = 0; x < BTW; ++x) acc[x] ^= sG[(8 * tau + bq) * BTW + x] & msk;
-                    }
-#pragma unroll
-                    for (int x = 0; x < BTW; ++x) T[(size_t)e2 * BTW + x] = acc[x];
-                }
-                __syncthreads();
-                for (int64_t off = tid; off < rows; off += BATCH_THREADS) {
-                    const int k = (off <= maxpos) ? smap[off] : -1;
-                    const uint64_t *src = (k >= 0) ? S + (int64_t)k * ldS : A + (r + off) * ld;
-                    uint64_t *dst = A + (r + off) * ld;
-                    const uint64_t ix = idx[off];
-                    uint64_t acc[BTW];
-#pragma unroll
-                    for (int x = 0; x < BTW; ++x) {
-                        const int64_t w = wbase + x;
-                        acc[x] = (w >= w_lo && w < W) ? src[w] : 0ull;
-                    }
-#pragma unroll
-                    for (int tau = 0; tau < NTAB; ++tau) {
-                        const int e = (int)((ix >> (8 * tau)) & 255ull);
-                        const uint64_t *te = T + ((size_t)tau * 256 + e) * BTW;
-#pragma unroll
-                        for (int x = 0; x < BTW; ++x) acc[x] ^= te[x];
-                    }
-#pragma unroll
-                    for (int x = 0; x < BTW; ++x) {
-                        const int64_t w = wbase + x;
-                        if (w >= w_lo && w < W) dst[w] = acc[x];
-                    }
-                }
-                __syncthreads();
+            // tabulated update of the words right of the stripe, in the
+            // configuration tuned for this matrix's size class
+            switch ((tune_bits >> (4 * batch_size_class(m, n))) & 15u) {
+            case 1: batch_tables_update<8, 1>(T, sG, S, ldS, A, ld, r, rows, W, cw + 1, rbar, smap, maxpos, idx); break;
+            case 2: batch_tables_update<4, 1>(T, sG, S, ldS, A, ld, r, rows, W, cw + 1, rbar, smap, maxpos, idx); break;
+            case 3: batch_tables_update<4, 2>(T, sG, S, ldS, A, ld, r, rows, W, cw + 1, rbar, smap, maxpos, idx); break;
+            case 4: batch_tables_update<4, 4>(T, sG, S, ldS, A, ld, r, rows, W, cw + 1, rbar, smap, maxpos, idx); break;
+            default: batch_tables_update<8, 2>(T, sG, S, ldS, A, ld, r, rows, W, cw + 1, rbar, smap, maxpos, idx); break;
             }
             // staged rows: their left part (old L bits, new L bits, stripe)
             for (int64_t t = tid; t < (int64_t)nS * (cw + 1); t += BATCH_THREADS) {
@@ -189,10 +224,38 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
     }
 }
 
+// Random Bernoulli(1/2) contents for tuning batches: splitmix64 of
+// (seed, matrix, word), padding bits cleared.
+__global__ void batch_fill_kernel(const gf2_batch_item *items, int count, uint64_t seed)
+{
+    for (int b = blockIdx.x; b < count; b += gridDim.x) {
+        const gf2_batch_item it = items[b];
+        const int64_t W = (it.n + 63) >> 6;
+        const uint64_t pad = (it.n & 63) ? ((1ull << (it.n & 63)) - 1ull) : ~0ull;
+        for (int64_t t = threadIdx.x; t < it.m * W; t += blockDim.x) {
+            const int64_t i = t / W, w = t - i * W;
+            uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(((int64_t)b << 32) + t + 1);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            it.A[i * it.ld_words + w] = (w == W - 1) ? (z & pad) : z;
+        }
+    }
+}
+
+cudaError_t launch_batch_fill(cudaStream_t st, const gf2_batch_item *items, int count, uint64_t seed, int num_sms)
+{
+    if (count <= 0) return cudaSuccess;
+    const int grid = count < 8 * num_sms ? count : 8 * num_sms;
+    batch_fill_kernel<<<grid, 256, 0, st>>>(items, count, seed);
+    return cudaGetLastError();
+}
+
 size_t batched_smem_bytes() { return (size_t)BTAB_WORDS * sizeof(uint64_t); }
 
 cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const int32_t *order, int count,
-                           int32_t *next, uint64_t *scratch, int64_t max_rows, int64_t ldS, int grid)
+                           int32_t *next, uint64_t *scratch, int64_t max_rows, int64_t ldS, int grid,
+                           BatchTune tune)
 {
     const size_t per_idx = (size_t)max_rows, per_S = (size_t)SMAX * ldS;
     BatchScratch scr;
@@ -203,7 +266,10 @@ cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const i
     scr.gval = scr.S + per_S * grid;
     scr.glb = scr.gval + per_idx * grid;
     scr.gsrc = reinterpret_cast<int32_t *>(scr.glb + per_idx * grid);
-    batched_ple_kernel<<<grid, BATCH_THREADS, batched_smem_bytes(), st>>>(items, order, count, next, scr);
+    uint32_t tune_bits = 0;                           // 4 bits per size class
+    for (int c = 0; c < BATCH_CLASSES; ++c) tune_bits |= (uint32_t)(tune.cfg[c] & 15) << (4 * c);
+    batched_ple_kernel<<<grid, BATCH_THREADS, batched_smem_bytes(), st>>>(items, order, count, next, scr,
+                                                                          tune_bits);
     return cudaGetLastError();
 }
 

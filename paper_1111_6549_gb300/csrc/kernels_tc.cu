@@ -1,0 +1,336 @@
+// kernels_tc.cu -- the trailing update / product on the 5th-generation tensor
+// cores (tcgen05), exact over GF(2).
+//
+// For a tile of 128 rows x 256 columns: D = X * G^T counts, over GF(2)
+// generators G (K rows of 256 column bits) and per-row coefficient words X
+// (K bits per row), and the row's bits flip where the count is odd:
+//     row[col] ^= parity( sum_k X[row][k] * G[k][col] ).
+// This is the same update as the tabulated one (Section 3.2's A22 += L21 A12,
+// or C ^= A B), computed as an integer matrix product and reduced mod 2, which
+// is exact because every operand is 0 or 1 and every count stays below 2^23.
+//
+//  * operands: 0/1 as FP8 E4M3 (1.0 = 0x38), both K-major, in the canonical
+//    no-swizzle layout of 8-row x 16-byte core matrices (K-direction stride
+//    128 bytes, row-direction stride 512 bytes for a 64-byte K chunk);
+//  * one elected thread issues tcgen05.mma (kind::f8f6f4, M = 128, N = 256,
+//    K = 32 per instruction) into a 256-column fp32 accumulator in tensor
+//    memory, and tcgen05.commit signals an mbarrier;
+//  * the epilogue reads the counts with tcgen05.ld (32 lanes x 32 columns per
+//    warp and instruction), takes the parity by adding 2^23 (the integer then
+//    sits in the low mantissa bits) and packs 64 parities per word.
+// Every mbarrier wait is bounded; on expiry the kernel records GF2_ETIMEOUT in
+// the error word, frees its tensor memory and returns.
+#include "common.cuh"
+
+namespace gf2 {
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_M = 128;
+constexpr int TC_N = 256;
+constexpr int TC_KC = 64;                                   // K chunk: 64 generators
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr uint32_t TC_IDESC = (1u << 4)                     // D: f32
+                              | (0u << 7) | (0u << 10)      // A, B: E4M3
+                              | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+constexpr int TC_A_BYTES = TC_M * TC_KC;                    // 8 KiB
+constexpr int TC_B_BYTES = TC_N * TC_KC;                    // 16 KiB
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s: far beyond any product here
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase, giving up after TC_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
+{
+    const unsigned long long t0 = gtime();
+    while (!mbar_try_wait(bar, phase))
+        if (gtime() - t0 > TC_WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start, K-direction and row-direction core
+// matrix strides (bytes), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned transpose32_tc(unsigned x)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const unsigned m = masks[k];
+        const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+// Byte offset of (row, 16-byte K group j) in the core-matrix layout of a
+// 64-byte-per-row K chunk.
+__device__ __forceinline__ uint32_t core_off(int row, int j) { return (uint32_t)(((row >> 3) * 4 + j) * 128 + (row & 7) * 16); }
+
+// 64 bits -> 64 E4M3 bytes (1.0 where the bit is set), as four 16-byte groups.
+__device__ __forceinline__ void expand_store(uint8_t *tile, int row, uint64_t bits, const uint64_t *lut)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint64_t lo = lut[(bits >> (16 * j)) & 255u];
+        const uint64_t hi = lut[(bits >> (16 * j + 8)) & 255u];
+        *reinterpret_cast<ulonglong2 *>(tile + core_off(row, j)) = make_ulonglong2(lo, hi);
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_update_kernel(UpdArgs a)
+{
+    __shared__ __align__(1024) uint8_t sA[TC_A_BYTES];
+    __shared__ __align__(1024) uint8_t sB[TC_B_BYTES];
+    __shared__ uint64_t lut[256];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ const uint64_t *sGen[KS];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const StripeDesc *d = a.desc;
+    int64_t row_lo, row_hi, w_lo, r = 0;
+    int maxpos = -1, nS = 0, nchunks = 1;
+    const int64_t W = a.W;
+    if (a.mode == UPD_PLE) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        r = d->r;
+        row_lo = r;
+        row_hi = a.m;
+        w_lo = (d->c >> 6) + 1;
+        maxpos = d->maxpos;
+        nS = d->nS;
+        if (tid < KS) sGen[tid] = (tid < rbar) ? a.S + tid * a.ldS : nullptr;
+    } else if (a.mode == UPD_RREF) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        row_lo = 0;
+        row_hi = d->r;
+        w_lo = d->c >> 6;
+        if (tid < KS) sGen[tid] = nullptr;
+        __syncthreads();
+        if (tid < rbar) sGen[d->qbar[tid]] = a.A + (d->r + tid) * a.ld;
+    } else {
+        row_lo = a.row_lo;
+        row_hi = a.row_hi;
+        w_lo = a.w_lo;
+        nchunks = (int)((a.gen_count + TC_KC - 1) / TC_KC);
+    }
+    // E4M3 expansion of a byte: 0x38 (1.0) in every byte whose bit is set
+    for (int b = tid; b < 256; b += TC_THREADS) {
+        uint64_t v = 0;
+        for (int i = 0; i < 8; ++i)
+            if ((b >> i) & 1) v |= 0x38ull << (8 * i);
+        lut[b] = v;
+    }
+    if (tid == 0) { mbar_init(&mbar, 1); s_abort = 0; }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(&tmem_base)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    // PLE: staged rows get their left part (old L bits, new L bits, stripe)
+    if (a.mode == UPD_PLE && a.left_copies) {
+        for (int k = blockIdx.x; k < nS; k += gridDim.x) {
+            const uint64_t *src = a.S + (int64_t)k * a.ldS;
+            uint64_t *dst = a.A + (r + d->S_off[k]) * a.ld;
+            for (int64_t w = tid; w < w_lo; w += TC_THREADS) dst[w] = src[w];
+        }
+    }
+
+    const int64_t R = row_hi - row_lo;
+    uint32_t phase = 0;
+    if (R > 0 && w_lo < W) {
+        const int64_t x0 = w_lo / 4, x1 = (W + 3) / 4;     // 256-column tiles, word aligned
+        const int64_t NTX = x1 - x0, NTY = (R + TC_M - 1) / TC_M;
+        const int64_t T = NTX * NTY;
+        const int64_t t_beg = T * blockIdx.x / gridDim.x, t_end = T * (blockIdx.x + 1) / gridDim.x;
+        if (blockIdx.x == 0 && tid == 0 && a.bytes)
+            atomicAdd(a.bytes, (unsigned long long)(R * (W - w_lo) * 16));
+        int64_t b_tile = -1;                               // tile whose generators sit in sB
+        for (int64_t t = t_beg; t < t_end; ++t) {
+            const int64_t tx = x0 + t / NTY, ty = t % NTY;
+            const int64_t wb = tx * 4;
+            const int64_t row0 = row_lo + ty * TC_M;
+            for (int kc = 0; kc < nchunks; ++kc) {
+                // ---- operands: coefficient rows -> sA, generators -> sB
+                {
+                    const int64_t i = row0 + tid;
+                    uint64_t x = 0;
+                    if (i < row_hi) x = (a.mode == UPD_MUL) ? a.idx[i * a.idx_stride + kc] : a.idx[i * a.idx_stride];
+                    if (a.mode == UPD_MUL) {
+                        const int64_t rem = a.gen_count - (int64_t)kc * TC_KC;
+                        if (rem < 64) x &= (rem <= 0) ? 0ull : ((1ull << rem) - 1ull);
+                    }
+                    expand_store(sA, tid, x, lut);
+                }
+                if (a.mode == UPD_MUL || b_tile != tx) {
+                    // warp w transposes generator word wb + w (64 columns) over 64 generators
+                    const int64_t word = wb + warp;
+                    uint64_t g0 = 0, g1 = 0;
+                    if (word < W) {
+                        if (a.mode == UPD_MUL) {
+                            const int64_t k0 = (int64_t)kc * TC_KC;
+                            if (k0 + lane < a.gen_count) g0 = a.B[(k0 + lane) * a.ldb + word];
+                            if (k0 + 32 + lane < a.gen_count) g1 = a.B[(k0 + 32 + lane) * a.ldb + word];
+                        } else {
+                            const uint64_t *p0 = sGen[lane], *p1 = sGen[32 + lane];
+                            if (p0) g0 = p0[word];
+                            if (p1) g1 = p1[word];
+                        }
+                    }
+                    const unsigned c0a = transpose32_tc((unsigned)g0), c1a = transpose32_tc((unsigned)(g0 >> 32));
+                    const unsigned c0b = transpose32_tc((unsigned)g1), c1b = transpose32_tc((unsigned)(g1 >> 32));
+                    // lane c: column 64w + c and 64w + 32 + c, 64 generator bits each
+                    expand_store(sB, warp * 64 + lane, ((uint64_t)c0b << 32) | c0a, lut);
+                    expand_store(sB, warp * 64 + 32 + lane, ((uint64_t)c1b << 32) | c1a, lut);
+                    b_tile = tx;
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint32_t a0 = saddr(sA), b0 = saddr(sB);
+#pragma unroll
+                    for (int ks = 0; ks < TC_KC / 32; ++ks)
+                        mma_f8(tmem, smem_desc(a0 + ks * 256, 128, 512), smem_desc(b0 + ks * 256, 128, 512),
+                               (kc > 0 || ks > 0) ? 1u : 0u);
+                    mma_commit(&mbar);
+                }
+                // all threads wait for the products (the operand buffers are reused next)
+                if (!mbar_wait_bounded(&mbar, phase)) {
+                    s_abort = 1;
+                    if (a.err) atomicExch(a.err, 4);   // GF2_ETIMEOUT
+                }
+                __syncthreads();                             // one decision for the whole block
+                if (s_abort) break;
+                phase ^= 1u;
+                tc_fence_after();
+            }
+            if (s_abort) break;
+            // ---- epilogue: parity of the counts, XOR into the rows
+            const int64_t i = row0 + warp * 32 + lane;
+            const uint64_t *src = nullptr;
+            uint64_t *dst = nullptr;
+            if (i < row_hi) {
+                src = a.A + i * a.ld;
+                if (a.mode == UPD_PLE && i - r <= maxpos) {
+                    const int mv = a.map[i];
+                    if (mv >= 0 && (mv >> 8) == a.stripe) src = a.S + (int64_t)(mv & 255) * a.ldS;
+                }
+                dst = a.A + i * a.ld;
+            }
+#pragma unroll 1
+            for (int cb = 0; cb < 8; cb += 2) {
+                uint32_t v0[32], v1[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), v0);
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((cb + 1) * 32), v1);
+                uint32_t p0 = 0, p1 = 0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    p0 |= (__float_as_uint(__uint_as_float(v0[q]) + 8388608.0f) & 1u) << q;
+                    p1 |= (__float_as_uint(__uint_as_float(v1[q]) + 8388608.0f) & 1u) << q;
+                }
+                const int64_t w = wb + cb / 2;
+                if (dst && w >= w_lo && w < W) dst[w] = src[w] ^ (((uint64_t)p1 << 32) | p0);
+            }
+            tc_fence_before();
+            __syncthreads();                                 // TMEM and sA free for the next tile
+            tc_fence_after();
+        }
+    }
+    if (s_abort) {
+        // the last product may still be running: wait for it (bounded) before
+        // its tensor memory is released
+        mbar_wait_bounded(&mbar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+cudaError_t launch_update_tc(cudaStream_t st, const UpdArgs &a, int num_sms)
+{
+    const int grid = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
+    tc_update_kernel<<<grid, TC_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gf2

@@ -1,0 +1,59 @@
+"""The tensor-core (tcgen05) forms of the product and of the trailing
+updates: bit-exact against the oracle, like the table forms."""
+import numpy as np
+import pytest
+
+import gf2inputs as gi
+import oracle
+from tests.gpu_util import to_dev, to_host, vec_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    hh.set_option(g.OPT_TC_MUL, 1)
+    return hh
+
+
+@pytest.mark.parametrize("m,k,n", [(128, 64, 256), (1, 1, 1), (300, 70, 300), (129, 65, 257),
+                                   (1000, 1000, 1000), (513, 2049, 300), (64, 0, 64), (2048, 130, 4100)])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_tc_mul(h, m, k, n, accumulate):
+    A = gi.bernoulli_matrix(m, k, 11) if k else np.zeros((m, 1), np.uint64)
+    B = gi.bernoulli_matrix(k, n, 12) if k else np.zeros((1, gi.words_for(n)), np.uint64)
+    C0 = gi.bernoulli_matrix(m, n, 13)
+    dC = to_dev(C0)
+    h.mul(dC, to_dev(A), to_dev(B), m, k, n, accumulate=accumulate)
+    want = C0.copy() if accumulate else np.zeros_like(C0)
+    if k:
+        oracle.mul(A, B, m, k, n, C=want, accumulate=accumulate)
+    assert np.array_equal(to_host(dC), want)
+
+
+@pytest.mark.parametrize("kind,m,n", [("dense", 300, 300), ("dense", 1000, 1500), ("lowrank", 700, 900),
+                                      ("dense", 2048, 2048)])
+def test_tc_update_ple_and_rref(kind, m, n):
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    hh.set_option(g.OPT_TC_UPDATE, 1)
+    if kind == "dense":
+        A = gi.bernoulli_matrix(m, n, m + n)
+    else:
+        k = min(m, n) // 3
+        A = oracle.mul(gi.bernoulli_matrix(m, k, 1), gi.bernoulli_matrix(k, n, 2), m, k, n)
+    dA = to_dev(A)
+    P, Q = vec_dev(m), vec_dev(min(m, n))
+    r = hh.ple(dA, m, n, P, Q)
+    LE = A.copy()
+    r0, P0, Q0 = oracle.ple(LE, m, n)
+    assert r == r0
+    assert np.array_equal(P.cpu().numpy()[:m], P0) and np.array_equal(Q.cpu().numpy()[:min(m, n)], Q0)
+    assert np.array_equal(to_host(dA, gi.words_for(n)), LE)
+    dR = to_dev(A)
+    r2 = hh.rref(dR, m, n, Q)
+    R0 = A.copy()
+    oracle.rref(R0, m, n)
+    assert r2 == r0 and np.array_equal(to_host(dR, gi.words_for(n)), R0)
