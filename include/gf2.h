@@ -277,11 +277,19 @@ int gf2_server_destroy(gf2_server_t server);
  *                      counts accumulated in tensor memory and reduced mod 2
  *   GF2_OPT_TC_UPDATE  the PLE / RREF trailing updates on the tensor cores
  *                      instead of the Four-Russians tables
+ *   GF2_OPT_TMA_UPDATE the table updates move their rows between HBM and
+ *                      shared memory by TMA (a producer warp, five stages)
+ *                      where the matrix allows it (16-byte aligned base, even
+ *                      ld_words, at least 16 words and 256 rows)
+ * Look-ahead is on by default; the tensor-core and TMA forms are off (the
+ * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
+ * GF2_EINVAL for an unknown option.
  */
-#define GF2_OPT_LOOKAHEAD 1
-#define GF2_OPT_TC_MUL    2
-#define GF2_OPT_TC_UPDATE 3
+#define GF2_OPT_LOOKAHEAD  1
+#define GF2_OPT_TC_MUL     2
+#define GF2_OPT_TC_UPDATE  3
+#define GF2_OPT_TMA_UPDATE 4
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */

@@ -24,7 +24,7 @@ __all__ = ["Handle", "GF2Error", "load", "lib_path", "SOLVE_UNIQUE", "SOLVE_UNDE
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
-OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE = 1, 2, 3
+OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE, OPT_TMA_UPDATE = 1, 2, 3, 4
 BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
 
@@ -309,7 +309,7 @@ class Handle:
         return rank.value
 
     def set_option(self, option: int, value: int) -> None:
-        """OPT_LOOKAHEAD / OPT_TC_MUL / OPT_TC_UPDATE (0 off, 1 on); results are identical."""
+        """OPT_LOOKAHEAD / OPT_TC_MUL / OPT_TC_UPDATE / OPT_TMA_UPDATE (0 off, 1 on); results are identical."""
         _check(load().gf2_set_option(self._h, option, int(value)), "gf2_set_option")
 
     # ---- statistics -----------------------------------------------------

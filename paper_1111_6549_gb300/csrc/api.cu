@@ -43,6 +43,11 @@ struct gf2_handle {
     std::vector<Pending> ev_pending;
     double kind_ms[5] = {0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other
     BatchTune btune{};             // batched kernel: table configuration per size class
+    bool tma = false;              // update rows move by TMA where A allows it (measured slower)
+    TensorMap2D tmap{};            // TMA descriptor of the last updated matrix
+    const void *tm_A = nullptr;
+    int64_t tm_m = -1, tm_W = -1, tm_ld = -1;
+    bool tm_ok = false;
 };
 
 namespace {
@@ -175,6 +180,18 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
     UpdArgs a = a_in;
     a.err = err_dev(h);
     const bool tc = (a.mode == UPD_MUL) ? h->tc_mul : h->tc_update;
+    a.tmap = nullptr;
+    if (!tc && h->tma) {
+        const int64_t rows = (a.mode == UPD_MUL) ? a.row_hi : a.m;
+        if (a.A != h->tm_A || rows != h->tm_m || a.W != h->tm_W || a.ld != h->tm_ld) {
+            h->tm_ok = encode_row_tiles(&h->tmap, a.A, rows, a.W, a.ld);
+            h->tm_A = a.A;
+            h->tm_m = rows;
+            h->tm_W = a.W;
+            h->tm_ld = a.ld;
+        }
+        if (h->tm_ok) a.tmap = &h->tmap;
+    }
     if (tc) CK(launch_update_tc(h->stream, a, h->num_sms));
     else CK(launch_update(h->stream, a, h->num_sms));
     h->launches += 1;
@@ -1035,6 +1052,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
     case GF2_OPT_LOOKAHEAD: h->lookahead = value != 0; return GF2_OK;
     case GF2_OPT_TC_MUL: h->tc_mul = value != 0; return GF2_OK;
     case GF2_OPT_TC_UPDATE: h->tc_update = value != 0; return GF2_OK;
+    case GF2_OPT_TMA_UPDATE: h->tma = value != 0; return GF2_OK;
     default: return GF2_EINVAL;
     }
 }

@@ -102,7 +102,17 @@ struct UpdArgs {
     int left_copies;           // PLE: also write the staged rows' left parts
     int grid;                  // CTAs to launch (0: one per SM)
     int32_t *err;              // device error word (bounded waits that expire), may be null
+    const struct TensorMap2D *tmap;  // TMA descriptor of A's rows (null: plain loads and stores)
 };
+
+// A CUtensorMap (128 bytes) kept opaque outside the files that use TMA.
+struct alignas(64) TensorMap2D {
+    unsigned char bytes[128];
+};
+// Encode the TMA descriptor of an m x W word matrix with row stride ld words
+// for the update kernel's 64-byte x 256-row boxes; false when A is not
+// eligible (base not 16-byte aligned, odd ld, fewer than 16 words or 256 rows).
+bool encode_row_tiles(TensorMap2D *out, const uint64_t *A, int64_t m, int64_t W, int64_t ld);
 
 // ---- launchers (host side, defined in the .cu files) ----
 cudaError_t launch_init_ple(cudaStream_t st, int64_t *P, int64_t *Q, int64_t m, int64_t qn,
