@@ -55,18 +55,28 @@ def peaks():
         return 6800.0, "fallback"
 
 
+UPDATE_SOURCES = ("kernels_update.cu", "tables_dev.cuh", "common.cuh")
+
+
+def update_kernel_digest() -> str:
+    h = hashlib.sha256()
+    for name in UPDATE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1111_6549_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def update_kernel_traffic():
-    """Per-launch DRAM traffic of the update kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_1111_6549_gb300", "csrc", "kernels_update.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """DRAM bytes per algorithmic byte of the update kernel, from the committed
+    ncu summary, if it was taken on the current kernel sources (else None)."""
+    digest = update_kernel_digest()
     for path in glob.glob(os.path.join(ROOT, "profiles", "update_kernel*.md")):
         text = open(path).read()
         mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-        mt = re.search(r"traffic_bytes_per_launch_65536:\s*([0-9.eE+]+)", text)
+        mt = re.search(r"dram_bytes_per_algorithmic_byte:\s*([0-9.eE+]+)", text)
         if mh and mt and mh.group(1) == digest:
-            return float(mt.group(1))
-    return None
+            return float(mt.group(1)), os.path.relpath(path, ROOT)
+    return None, None
 
 
 class ClockSampler:
@@ -478,11 +488,15 @@ def run_ours(args):
     hbm, hbm_kind = peaks()
     upd_gbs = st["update_bytes"] / (st["update_ms"] / 1e3) / 1e9 if st["update_ms"] > 0 else None
     upd_per_launch_bytes = st["update_bytes"] / max(st["update_launches"], 1)
-    traffic = update_kernel_traffic()
+    ratio, ratio_src = update_kernel_traffic()
+    traffic = ratio * upd_per_launch_bytes if ratio is not None else None
     roofline = {"kernel": "update_kernel (tabulated trailing update, PLE + RREF passes)",
                 "bound": "hbm", "achieved": upd_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (upd_gbs / hbm) if upd_gbs else None, "peak_kind": hbm_kind,
                 "traffic": traffic, "algorithmic_bytes_per_launch": upd_per_launch_bytes,
+                "traffic_source": (f"{ratio_src}: ncu dram__bytes_read.sum + dram__bytes_write.sum over "
+                                   f"the update launches of a 32768^2 capture, {ratio:.3f} DRAM bytes per "
+                                   f"algorithmic byte, scaled to this launch size") if ratio else None,
                 "launches_per_step": st["update_launches"] / args.steps,
                 "update_share_of_step": st["update_ms"] / ms if ms > 0 else None,
                 "kernel_ms_per_step_diagnostic": {k: sd[k + "_ms"] / diag_steps

@@ -127,6 +127,8 @@ cudaError_t setup_update_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
 bool update_vectorised(const UpdArgs &a);   // true when the paired, pipelined form runs
 cudaError_t launch_update_tc(cudaStream_t st, const UpdArgs &a, int num_sms);
+cudaError_t setup_update_tma_kernel();
+cudaError_t launch_update_tma(cudaStream_t st, const UpdArgs &a, int grid);   // a.tmap must be set
 cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t W, int64_t ld,
                                const int64_t *r_dev, int num_sms);
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
