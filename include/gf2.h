@@ -305,8 +305,11 @@ typedef struct gf2_stats {
     double  prep_ms;              /* by kind (only while profiling is on)      */
     double  rref_prep_ms;
     double  other_ms;
+    int64_t update_timed_launches;/* update launches timed while profiling     */
 } gf2_stats;
-/* Per-launch event timing: 0 off, 1 the update kernel only, 2 every kernel. */
+/* Per-launch event timing: 0 off, 1 the update kernel only, 2 every kernel,
+   3 every 7th update launch (only those add to update_ms and update_bytes).
+   While profiling is off update_bytes counts every update launch. */
 int gf2_set_profiling(gf2_handle_t handle, int on);
 /* Read the counters (synchronises the stream to finish the event timing). */
 int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);

@@ -40,7 +40,7 @@ class _Stats(ctypes.Structure):
                 ("update_ms", ctypes.c_double), ("update_bytes", ctypes.c_double),
                 ("panel_fallbacks", ctypes.c_int64), ("panel_ms", ctypes.c_double),
                 ("prep_ms", ctypes.c_double), ("rref_prep_ms", ctypes.c_double),
-                ("other_ms", ctypes.c_double)]
+                ("other_ms", ctypes.c_double), ("update_timed_launches", ctypes.c_int64)]
 
 
 class SolveJob(ctypes.Structure):
@@ -314,7 +314,8 @@ class Handle:
 
     # ---- statistics -----------------------------------------------------
     def set_profiling(self, level) -> None:
-        """0: off, 1 (or True): time the update kernel, 2: time every kernel."""
+        """0: off, 1 (or True): time the update kernel, 2: time every kernel,
+        3: time every 7th update launch (only those count in update_ms/update_bytes)."""
         _check(load().gf2_set_profiling(self._h, int(level)), "gf2_set_profiling")
 
     def stats(self) -> dict:

@@ -37,7 +37,8 @@ struct gf2_handle {
     char *small = nullptr;     // rank, flags, counters
     int64_t launches = 0;
     int64_t upd_launches = 0;
-    int profiling = 0;             // 1: time update launches, 2: time every launch
+    int profiling = 0;             // 1: time update launches, 2: every launch, 3: every 7th update launch
+    int64_t upd_timed = 0;         // update launches timed (and counted in the byte counter)
     std::vector<cudaEvent_t> ev_free;
     struct Pending { cudaEvent_t e0, e1; int kind; };
     std::vector<Pending> ev_pending;
@@ -150,10 +151,10 @@ struct Timed {
     int kind;
     cudaStream_t st;
     cudaEvent_t e0 = nullptr;
-    Timed(gf2_handle *h_, int kind_, cudaStream_t st_ = nullptr)
+    Timed(gf2_handle *h_, int kind_, cudaStream_t st_ = nullptr, bool enable = true)
         : h(h_), kind(kind_), st(st_ ? st_ : h_->stream)
     {
-        if (h->profiling == 0 || (h->profiling == 1 && kind != K_UPDATE)) return;
+        if (!enable || h->profiling == 0 || (h->profiling != 2 && kind != K_UPDATE)) return;
         e0 = take();
         if (e0) cudaEventRecord(e0, st);
     }
@@ -174,10 +175,19 @@ struct Timed {
     }
 };
 
+// Profiling level 3 samples every UPD_SAMPLE-th update launch (odd, so both
+// halves of the look-ahead split are sampled): only those are bracketed by
+// events and add to the byte counter, which keeps the event overhead out of
+// the timed steps while the ratio bytes / time still covers the whole run.
+constexpr int64_t UPD_SAMPLE = 7;
+
 int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
 {
-    Timed t(h, K_UPDATE);
+    const bool timed = h->profiling != 3 || h->upd_launches % UPD_SAMPLE == 0;
+    Timed t(h, K_UPDATE, nullptr, timed);
     UpdArgs a = a_in;
+    if (!timed) a.bytes = nullptr;
+    else if (h->profiling) h->upd_timed += 1;
     a.err = err_dev(h);
     const bool tc = (a.mode == UPD_MUL) ? h->tc_mul : h->tc_update;
     a.tmap = nullptr;
@@ -1060,7 +1070,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
 int gf2_set_profiling(gf2_handle_t h, int on)
 {
     if (!h) return GF2_EINVAL;
-    h->profiling = on < 0 ? 0 : (on > 2 ? 2 : on);
+    h->profiling = on < 0 ? 0 : (on > 3 ? 3 : on);
     return GF2_OK;
 }
 
@@ -1083,6 +1093,7 @@ int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
     CK(cudaMemcpy(&fb, fb_dev(h), 4, cudaMemcpyDeviceToHost));
     out->kernel_launches = h->launches;
     out->update_launches = h->upd_launches;
+    out->update_timed_launches = h->upd_timed;
     out->update_ms = h->kind_ms[K_UPDATE];
     out->panel_ms = h->kind_ms[K_PANEL];
     out->prep_ms = h->kind_ms[K_PREP];
@@ -1102,6 +1113,7 @@ int gf2_reset_stats(gf2_handle_t h)
     h->ev_pending.clear();
     h->launches = 0;
     h->upd_launches = 0;
+    h->upd_timed = 0;
     for (double &x : h->kind_ms) x = 0.0;
     CK(cudaMemset(h->small + SM_FALLBACK, 0, 12));
     return GF2_OK;

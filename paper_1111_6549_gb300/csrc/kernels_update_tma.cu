@@ -27,7 +27,7 @@ namespace gf2 {
 // instead of the TMA store.
 constexpr int TMA_ROWS = 256;                        // rows per batch = one box
 constexpr int TMA_STAGE_BYTES = TMA_ROWS * TW * 8;   // 16 KiB
-constexpr int TMA_STAGES = 5;
+constexpr int TMA_STAGES = 5;                       // 3 loads in flight, 1 updated, 1 stored
 constexpr int WS_CONSUMER_WARPS = UPD_THREADS / 32;  // 16
 constexpr int WS_THREADS = UPD_THREADS + 32;         // + the producer warp
 constexpr size_t TMA_SMEM_BYTES = (size_t)TAB_WORDS * 8 + (size_t)TMA_STAGES * TMA_STAGE_BYTES + 128;
@@ -134,42 +134,42 @@ update_tma_kernel(UpdArgs a, const __grid_constant__ TensorMap2D tm)
     if (tid >= UPD_THREADS) {
         // ---------------- producer warp: lane 0 issues every copy
         if (tid != UPD_THREADS) return;
-        int64_t issued = 0;
-        for (int64_t k = 0; k < nunits; ++k) {
-            const int st = (int)(k % TMA_STAGES);
-            if (k >= TMA_STAGES) {
-                const int64_t kp = k - TMA_STAGES;     // the batch that held this stage
-                if (s_abort || !mbar_wait_limited(&empty[st], (uint32_t)((kp / TMA_STAGES) & 1))) {
-                    s_abort = 1;
-                    if (a.err) atomicExch(a.err, 4);  // GF2_ETIMEOUT
-                    break;
+        // Loads run up to TMA_STAGES - 2 batches ahead of the batch being
+        // released, so the stage a load reuses was released (and its store
+        // committed) at least two batches earlier: its store has normally
+        // finished reading shared memory and the wait below does not block.
+        int64_t k_load = 0, issued = 0;
+        for (int64_t k_rel = 0; k_rel <= nunits; ++k_rel) {
+            const int64_t lim = min(nunits, k_rel + TMA_STAGES - 1);
+            while (k_load < lim) {
+                const int st = (int)(k_load % TMA_STAGES);
+                if (k_load >= TMA_STAGES) {
+                    const int64_t j = k_load - TMA_STAGES;      // the batch that held this stage
+                    if (unit_tma_out(u_beg + j)) {
+                        int later = 0;                          // stores committed after batch j's
+                        for (int64_t t = j + 1; t < k_rel; ++t) later += unit_tma_out(u_beg + t) ? 1 : 0;
+                        if (later <= 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                        else if (later == 1) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                        else if (later == 2) asm volatile("cp.async.bulk.wait_group.read 2;\n" ::: "memory");
+                        else asm volatile("cp.async.bulk.wait_group.read 3;\n" ::: "memory");
+                    }
                 }
-                if (unit_tma_out(u_beg + kp)) {
-                    tma_store_2d(&tm, (int)unit_x(u_beg + kp), (int)unit_row0(u_beg + kp),
-                                 stage + st * TMA_STAGE_BYTES);
-                    bulk_commit();
-                    bulk_wait_read_all();             // the store has read the stage
-                }
+                mbar_expect_tx(&full[st], TMA_STAGE_BYTES);
+                tma_load_2d(stage + st * TMA_STAGE_BYTES, &tm, (int)unit_x(u_beg + k_load),
+                            (int)unit_row0(u_beg + k_load), &full[st]);
+                issued = ++k_load;
             }
-            mbar_expect_tx(&full[st], TMA_STAGE_BYTES);
-            tma_load_2d(stage + st * TMA_STAGE_BYTES, &tm, (int)unit_x(u_beg + k), (int)unit_row0(u_beg + k),
-                        &full[st]);
-            issued = k + 1;
-        }
-        if (!s_abort) {
-            // the last batches: store each once the consumers release it
-            for (int64_t k = (nunits > TMA_STAGES ? nunits - TMA_STAGES : 0); k < nunits; ++k) {
-                const int st = (int)(k % TMA_STAGES);
-                if (!mbar_wait_limited(&empty[st], (uint32_t)((k / TMA_STAGES) & 1))) {
-                    s_abort = 1;
-                    if (a.err) atomicExch(a.err, 4);
-                    break;
-                }
-                if (unit_tma_out(u_beg + k)) {
-                    tma_store_2d(&tm, (int)unit_x(u_beg + k), (int)unit_row0(u_beg + k),
-                                 stage + st * TMA_STAGE_BYTES);
-                    bulk_commit();
-                }
+            if (k_rel == nunits) break;
+            const int st = (int)(k_rel % TMA_STAGES);
+            if (s_abort || !mbar_wait_limited(&empty[st], (uint32_t)((k_rel / TMA_STAGES) & 1))) {
+                s_abort = 1;
+                if (a.err) atomicExch(a.err, 4);              // GF2_ETIMEOUT
+                break;
+            }
+            if (unit_tma_out(u_beg + k_rel)) {
+                tma_store_2d(&tm, (int)unit_x(u_beg + k_rel), (int)unit_row0(u_beg + k_rel),
+                             stage + st * TMA_STAGE_BYTES);
+                bulk_commit();
             }
         }
         bulk_wait_all();                              // stores complete before the kernel ends
