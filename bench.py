@@ -289,6 +289,41 @@ def bench_batched(h, torch, dev, stream, reps: int = 5):
                          "chosen": chosen, "ms_per_class_and_config": tune_ms}}
 
 
+def bench_sparse(h, torch, dev, stream, weights=(1, 10, 40, 200), n=10000):
+    """The sparse workloads of Section 4's Figure: n x n with exactly w ones per
+    row at random columns; RREF via PLE (the paper's "PLE" times include the
+    RREF), CUDA-event median of 5 after 2 warm-ups."""
+    import gf2inputs as gi
+    out = {"workload": f"{n}x{n} GF(2), w nonzeros per row at uniform random distinct columns",
+           "paper_context": "Xeon E5345, one core (Figure): 0.97 s at w=1, peak ~1.32 s near w=33-41, "
+                            "0.72-0.75 s for w >= 120",
+           "points": []}
+    for w in weights:
+        A = gi.row_weight_matrix(n, n, w)
+        pristine = torch.from_numpy(A.view(np.int64)).to(dev)
+        work = torch.empty_like(pristine)
+        Q = torch.empty(n, dtype=torch.int64, device=dev)
+        rk = torch.zeros(1, dtype=torch.int64, device=dev)
+        times = []
+        for i in range(7):
+            work.copy_(pristine)
+            if i == 2:
+                h.reset_stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.rref_async(work, n, n, Q, rk)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                times.append(a.elapsed_time(b))
+        st = h.stats()
+        r = int(rk.cpu()[0])
+        t = statistics.median(times)
+        out["points"].append({"w": w, "rank": r, "ms": t, "gbitops": work_bits(n, n, r) / (t / 1e3) / 1e9,
+                              "block_panel_stripes_per_step": st["panel_fallbacks"] / 5})
+    return out
+
+
 def bench_served(h, torch, dev, rates=(200, 1000, 5000), jobs_per_rate=400, pool_size=48, slots=6):
     """The served solve workload: Poisson arrivals of gf2_solve jobs (n
     log-uniform in 128..16384, 1..64 right-hand sides) through the
@@ -603,6 +638,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and not args.no_batch:
         batched = bench_batched(h, torch, dev, stream)
+    sparse = None
+    if rank == 0 and not args.no_sparse:
+        sparse = bench_sparse(h, torch, dev, stream)
     served = None
     if rank == 0 and not args.no_serve:
         served = bench_served(h, torch, dev)
@@ -628,6 +666,7 @@ def run_ours(args):
                            "plain_path": "same kernels, one stripe after another on one stream "
                                          "(no look-ahead), one launch per panel step"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "served": served,
+                "sparse": sparse,
                 "gpu_launches": st["kernel_launches"], "clocks": clk.summary(),
                 "panel_fallbacks": st["panel_fallbacks"], "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
@@ -647,6 +686,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--tma", action="store_true",
                     help="run the update in its TMA-staged form (GF2_OPT_TMA_UPDATE)")
     ap.add_argument("--tc-compare", action="store_true",

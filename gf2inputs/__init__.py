@@ -180,6 +180,25 @@ def sparse_square(n: int, seed: int = BASE_SEED + 2) -> np.ndarray:
     return bernoulli_matrix(n, n, seed, density_log2=4)
 
 
+def row_weight_matrix(m: int, n: int, w: int, seed: int = BASE_SEED + 5) -> np.ndarray:
+    """m x n matrix with exactly w ones per row at uniformly random distinct
+    columns (the sparse workloads of Section 4's Figure: 10000 x 10000 with
+    1..200 nonzeros per row).  Floyd's sampling, one draw per row and step."""
+    assert 0 <= w <= n
+    W = words_for(n)
+    A = np.zeros((m, W), dtype=np.uint64)
+    rs = RowStreams(seed, m)
+    rows = np.arange(m)
+    one = np.uint64(1)
+    for j in range(n - w, n):
+        u = rs.next()
+        t = (u % np.uint64(j + 1)).astype(np.int64)
+        taken = (A[rows, t >> 6] >> (t & 63).astype(np.uint64)) & one
+        c = np.where(taken == one, j, t)
+        A[rows, c >> 6] |= one << (c & 63).astype(np.uint64)
+    return A
+
+
 def structured_factors(m: int = 16384, k: int = 8192, n: int = 32768,
                        seed: int = BASE_SEED + 2):
     """The two Bernoulli(1/2) factors X (m x k) and Y (k x n) of the rank-k workload.

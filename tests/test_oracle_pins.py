@@ -369,3 +369,18 @@ def test_batch_and_solve_recipes_shape():
     jobs = gi.solve_stream_recipe(50, rate=1000.0)
     assert all(128 <= j["n"] <= 16384 and 1 <= j["nrhs"] <= 64 for j in jobs)
     assert all(jobs[i]["t"] < jobs[i + 1]["t"] for i in range(49))
+
+
+def test_row_weight_generator_exact_weights():
+    """The sparse workload of Section 4's Figure: exactly w ones per row,
+    distinct columns, padding clear, deterministic per seed."""
+    for m, n, w in [(50, 70, 0), (50, 70, 1), (40, 130, 17), (30, 64, 64), (200, 1000, 40)]:
+        A = gi.row_weight_matrix(m, n, w, seed=9)
+        U = gi.unpack(A, m, n)
+        assert (U.sum(axis=1) == w).all()
+        assert np.array_equal(A, gi.row_weight_matrix(m, n, w, seed=9))
+        if n % 64:
+            assert not (A[:, -1] & np.uint64(~gi.pad_mask(n) & 0xFFFFFFFFFFFFFFFF)).any()
+    # columns are spread: every column of a 2000 x 100 draw with w = 50 is hit
+    U = gi.unpack(gi.row_weight_matrix(2000, 100, 50, seed=3), 2000, 100)
+    assert (U.sum(axis=0) > 700).all() and (U.sum(axis=0) < 1300).all()
