@@ -98,6 +98,22 @@ int gf2_rref_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64
                    int64_t *Q, int64_t *rank_dev);
 
 /*
+ * RREF by M4RI (Algorithm 8, Appendix A): the reduced row echelon form in one
+ * sweep over 64-column stripes.  Per stripe the pivots are found below the
+ * current rank with the rule of Algorithm 1 (leftmost column, first row,
+ * swaps), the stripe's pivot rows are fully reduced (GaussSubmatrix), and
+ * every other row -- above and below -- clears its bits in the pivot columns
+ * with one table lookup per 8 columns (MakeTable + AddRowsFromTable).
+ * Arguments, layout, ownership and errors as gf2_rref / gf2_rref_async; the
+ * result is the same unique RREF (Section 2), and Q[0..rank) the same pivot
+ * columns.  The tensor-core and TMA options do not apply to it.
+ */
+int gf2_rref_m4ri(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words, int64_t *Q,
+                  int64_t *rank);
+int gf2_rref_m4ri_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
+                        int64_t *Q, int64_t *rank_dev);
+
+/*
  * Product over GF(2) by tabulated row combinations (Section 3.2: the trailing
  * update is the M4RM multiplication of Albrecht, Bard & Hart; Algorithms 5-6).
  *   C = A B (accumulate = 0) or C ^= A B (accumulate != 0).

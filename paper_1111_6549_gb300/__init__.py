@@ -91,6 +91,8 @@ def load():
             "gf2_ple_async": ([vp, vp, i64, i64, i64, vp, vp, vp], ctypes.c_int),
             "gf2_rref": ([vp, vp, i64, i64, i64, vp, i64p], ctypes.c_int),
             "gf2_rref_async": ([vp, vp, i64, i64, i64, vp, vp], ctypes.c_int),
+            "gf2_rref_m4ri": ([vp, vp, i64, i64, i64, vp, i64p], ctypes.c_int),
+            "gf2_rref_m4ri_async": ([vp, vp, i64, i64, i64, vp, vp], ctypes.c_int),
             "gf2_mul": ([vp, vp, i64, vp, i64, vp, i64, i64, i64, i64, ctypes.c_int], ctypes.c_int),
             "gf2_solve": ([vp, vp, i64, i64, vp, i64, i64, i32p], ctypes.c_int),
             "gf2_ple_batched": ([vp, ctypes.POINTER(Desc), i64], ctypes.c_int),
@@ -218,6 +220,20 @@ class Handle:
         self._bind_stream()
         _check(load().gf2_rref_async(self._h, _dptr(A), m, n, ld, _dptr(Q), _dptr(rank_dev)),
                "gf2_rref_async")
+
+    def rref_m4ri(self, A, m: int, n: int, Q) -> int:
+        """RREF by M4RI (Algorithm 8), in place; returns the rank."""
+        ld = _mat(A, m, n)
+        self._bind_stream()
+        rank = ctypes.c_int64(0)
+        _check(load().gf2_rref_m4ri(self._h, _dptr(A), m, n, ld, _dptr(Q), ctypes.byref(rank)), "gf2_rref_m4ri")
+        return rank.value
+
+    def rref_m4ri_async(self, A, m: int, n: int, Q, rank_dev) -> None:
+        ld = _mat(A, m, n)
+        self._bind_stream()
+        _check(load().gf2_rref_m4ri_async(self._h, _dptr(A), m, n, ld, _dptr(Q), _dptr(rank_dev)),
+               "gf2_rref_m4ri_async")
 
     def mul(self, C, A, B, m: int, k: int, n: int, accumulate: bool = False) -> None:
         ldc = _mat(C, m, n)

@@ -75,7 +75,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int64_t words_for(int64_t n) { return (n + 63) >> 6; }
 
 struct Layout {
-    size_t descs, idx, map, S, gval, glb, gsrc, P, Q, total;
+    size_t descs, idx, map, S, G, gval, glb, gsrc, P, Q, total;
     int64_t ldS;
 };
 
@@ -91,9 +91,10 @@ Layout layout_for(int64_t m, int64_t ncols)
     L.idx = off;   off = align256(off + (size_t)mm * 8);
     L.map = off;   off = align256(off + (size_t)mm * 8);   // two halves, by stripe parity
     L.S = off;     off = align256(off + (size_t)SMAX * L.ldS * 8);
+    L.G = off;     off = align256(off + (size_t)KS * L.ldS * 8);     // M4RI: reduced pivot rows
     L.gval = off;  off = align256(off + (size_t)mm * 8);
     L.glb = off;   off = align256(off + (size_t)mm * 8);
-    L.gsrc = off;  off = align256(off + (size_t)mm * 4);
+    L.gsrc = off;  off = align256(off + (size_t)mm * 8);   // source offsets, then positions
     L.P = off;     off = align256(off + (size_t)mm * 8);
     L.Q = off;     off = align256(off + (size_t)std::max<int64_t>(std::min(m, ncols), 1) * 8);
     L.total = off;
@@ -189,9 +190,9 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
     if (!timed) a.bytes = nullptr;
     else if (h->profiling) h->upd_timed += 1;
     a.err = err_dev(h);
-    const bool tc = (a.mode == UPD_MUL) ? h->tc_mul : h->tc_update;
+    const bool tc = (a.mode == UPD_MUL) ? h->tc_mul : (a.mode == UPD_M4RI ? false : h->tc_update);
     a.tmap = nullptr;
-    if (!tc && h->tma) {
+    if (!tc && h->tma && a.mode != UPD_M4RI) {
         const int64_t rows = (a.mode == UPD_MUL) ? a.row_hi : a.m;
         if (a.A != h->tm_A || rows != h->tm_m || a.W != h->tm_W || a.ld != h->tm_ld) {
             h->tm_ok = encode_row_tiles(&h->tmap, a.A, rows, a.W, a.ld);
@@ -223,7 +224,8 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     int32_t *map = reinterpret_cast<int32_t *>(ws + L.map);
     uint64_t *S = reinterpret_cast<uint64_t *>(ws + L.S);
     PanelScratch gs{reinterpret_cast<uint64_t *>(ws + L.gval), reinterpret_cast<uint64_t *>(ws + L.glb),
-                    reinterpret_cast<int32_t *>(ws + L.gsrc)};
+                    reinterpret_cast<int32_t *>(ws + L.gsrc),
+                    reinterpret_cast<int32_t *>(ws + L.gsrc) + std::max<int64_t>(m, 1)};
     const int64_t qn = std::min(m, npiv);
     const int64_t W = words_for(ncols);
     const int64_t ns = words_for(npiv);
@@ -347,6 +349,67 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         a.bytes = bytes_dev(h);
         int rc = launch_update_counted(h, a);
         if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+// Enqueue M4RI (Algorithm 8): the RREF in one sweep over the stripes.  Per
+// stripe: the panel (pivot search below the rank, as for PLE), the reduced
+// pivot rows, staged rows and table indices (m4ri_prep), and the table update
+// of every row above and below.  The rank is left in r_dev, Q[0..rank) holds
+// the pivot columns.
+int run_m4ri(gf2_handle *h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q)
+{
+    const Layout L = layout_for(m, n);
+    int rc = grow(&h->ws, &h->ws_cap, L.total, h->stream);
+    if (rc) return rc;
+    char *ws = h->ws;
+    StripeDesc *descs = reinterpret_cast<StripeDesc *>(ws + L.descs);
+    uint64_t *IDX = reinterpret_cast<uint64_t *>(ws + L.idx);
+    int32_t *map = reinterpret_cast<int32_t *>(ws + L.map);
+    uint64_t *S = reinterpret_cast<uint64_t *>(ws + L.S);
+    uint64_t *G = reinterpret_cast<uint64_t *>(ws + L.G);
+    int64_t *P = reinterpret_cast<int64_t *>(ws + L.P);
+    PanelScratch gs{reinterpret_cast<uint64_t *>(ws + L.gval), reinterpret_cast<uint64_t *>(ws + L.glb),
+                    reinterpret_cast<int32_t *>(ws + L.gsrc),
+                    reinterpret_cast<int32_t *>(ws + L.gsrc) + std::max<int64_t>(m, 1)};
+    const int64_t W = words_for(n);
+    CK(cudaMemsetAsync(map, 0xFF, (size_t)std::max<int64_t>(m, 1) * 4, h->stream));
+    {
+        Timed t(h, K_OTHER);
+        CK(launch_init_ple(h->stream, P, Q, m, std::min(m, n), nullptr, r_dev(h), h->num_sms));
+    }
+    h->launches += 1;
+    for (int64_t s = 0; s < W; ++s) {
+        {
+            Timed t(h, K_PANEL);
+            CK(launch_panel(h->stream, A, m, ld, n, (int)s, descs, r_dev(h), P, Q, map, gs, fb_dev(h)));
+        }
+        {
+            Timed t(h, K_PREP);
+            CK(launch_m4ri_prep(h->stream, A, ld, W, (int)s, descs, map, S, L.ldS, G, IDX, m, h->num_sms));
+        }
+        h->launches += 2;
+        UpdArgs a{};
+        a.mode = UPD_M4RI;
+        a.A = A;
+        a.ld = ld;
+        a.m = m;
+        a.W = W;
+        a.desc = descs + s;
+        a.stripe = (int)s;
+        a.S = S;
+        a.ldS = L.ldS;
+        a.map = map;
+        a.idx = IDX;
+        a.idx_stride = 1;
+        a.B = G;
+        a.ldb = L.ldS;
+        a.bytes = bytes_dev(h);
+        a.tp_lo = 0;
+        a.tp_hi = -1;
+        a.left_copies = 1;
+        if ((rc = launch_update_counted(h, a))) return rc;
     }
     return GF2_OK;
 }
@@ -538,6 +601,38 @@ int gf2_rref_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld
         return GF2_OK;
     }
     rc = rref_enqueue(h, A, m, n, ld, Q);
+    if (rc) return rc;
+    CK(launch_copy_rank(h->stream, r_dev(h), rank_dev));
+    h->launches += 1;
+    return GF2_OK;
+}
+
+int gf2_rref_m4ri(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q, int64_t *rank)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (!rank || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    *rank = 0;
+    if (m == 0 || n == 0) return GF2_OK;
+    rc = run_m4ri(h, A, m, n, ld, Q);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(rank, r_dev(h), sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    return finish_sync(h);
+}
+
+int gf2_rref_m4ri_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q,
+                        int64_t *rank_dev)
+{
+    int rc = check_args(h, A, m, n, ld);
+    if (rc) return rc;
+    if (!rank_dev || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    if (m == 0 || n == 0) {
+        CK(cudaMemsetAsync(rank_dev, 0, 8, h->stream));
+        return GF2_OK;
+    }
+    rc = run_m4ri(h, A, m, n, ld, Q);
     if (rc) return rc;
     CK(launch_copy_rank(h->stream, r_dev(h), rank_dev));
     h->launches += 1;

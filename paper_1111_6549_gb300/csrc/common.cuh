@@ -71,13 +71,15 @@ __host__ __device__ inline int batch_size_class(int64_t m, int64_t n)
 }
 
 // Scratch of the block-wide panel path: one entry per remaining row.
+// Entries are the rows whose stripe word is nonzero, in position order.
 struct PanelScratch {
     uint64_t *val;   // stripe word, eliminated eagerly
     uint64_t *lb;    // L coefficient bits
-    int32_t *src;    // row offset (from r) whose content sits in this slot
+    int32_t *src;    // row offset (from r) whose content sits in this entry
+    int32_t *pos;    // current position offset of the entry (-1: taken as a pivot or retired)
 };
 
-enum UpdMode { UPD_PLE = 0, UPD_RREF = 1, UPD_MUL = 2 };
+enum UpdMode { UPD_PLE = 0, UPD_RREF = 1, UPD_MUL = 2, UPD_M4RI = 3 };
 
 struct UpdArgs {
     int mode;
@@ -92,7 +94,7 @@ struct UpdArgs {
     const int32_t *map;        // PLE: position -> stripe * 256 + staged slot, or -1
     const uint64_t *idx;       // table index per row (row i at idx[i * idx_stride])
     int64_t idx_stride;
-    const uint64_t *B;         // MUL: generator rows B + g * ldb
+    const uint64_t *B;         // MUL: generator rows B + g * ldb; M4RI: the reduced pivot rows
     int64_t ldb;
     int64_t gen_count;         // MUL: number of generator rows (<= 64)
     int64_t row_lo, row_hi;    // MUL: rows to update
@@ -134,6 +136,9 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
+cudaError_t launch_m4ri_prep(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int s,
+                             const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *G,
+                             uint64_t *IDX, int64_t m, int num_sms);
 cudaError_t launch_solve_status(cudaStream_t st, const int64_t *r_dev, const int32_t *flag, int64_t n,
                                 int32_t *status);
 cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const int32_t *order, int count,

@@ -133,7 +133,8 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
     uint64_t *idx = scr.idx + (size_t)blockIdx.x * scr.max_rows;
     uint64_t *S = scr.S + (size_t)blockIdx.x * SMAX * scr.ldS;
     PanelScratch gs{scr.gval + (size_t)blockIdx.x * scr.max_rows, scr.glb + (size_t)blockIdx.x * scr.max_rows,
-                    scr.gsrc + (size_t)blockIdx.x * scr.max_rows};
+                    scr.gsrc + (size_t)blockIdx.x * 2 * scr.max_rows,
+                    scr.gsrc + (size_t)blockIdx.x * 2 * scr.max_rows + scr.max_rows};
     const int64_t ldS = scr.ldS;
 
     for (;;) {
@@ -275,7 +276,9 @@ cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const i
 
 size_t batched_scratch_words(int64_t max_rows, int64_t ldS, int grid)
 {
-    return ((size_t)max_rows * 3 + (size_t)SMAX * ldS) * grid + ((size_t)max_rows * grid + 1) / 2 + 64;
+    // per CTA: index, panel values and L bits (8 B per row each), staged rows,
+    // panel sources and positions (2 x 4 B per row)
+    return ((size_t)max_rows * 4 + (size_t)SMAX * ldS) * grid + 64;
 }
 
 int batched_grid(int num_sms)

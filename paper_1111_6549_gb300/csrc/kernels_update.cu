@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
     int64_t row_lo, row_hi, w_lo;
     const int64_t W = a.W;
     int64_t r = 0;
-    int maxpos = -1, nS = 0;
+    int maxpos = -1, nS = 0, rbar_m = 0;
     const StripeDesc *d = a.desc;
     if (a.mode == UPD_PLE) {
         const int rbar = d->rbar;
@@ -63,6 +63,17 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
         if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
         __syncthreads();
         if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;
+    } else if (a.mode == UPD_M4RI) {
+        rbar_m = d->rbar;
+        if (rbar_m == 0) return;
+        r = d->r;
+        row_lo = 0;
+        row_hi = a.m;
+        w_lo = d->c >> 6;
+        maxpos = d->maxpos;
+        if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
+        __syncthreads();
+        if (threadIdx.x < rbar_m) sGen[d->qbar[threadIdx.x]] = a.B + threadIdx.x * a.ldb;
     } else {
         row_lo = a.row_lo;
         row_hi = a.row_hi;
@@ -72,6 +83,11 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
     }
     __syncthreads();
 
+    // M4RI: the pivot positions r .. r+rbar-1 take the reduced pivot rows
+    if (a.mode == UPD_M4RI) {
+        for (int p = blockIdx.x; p < rbar_m; p += gridDim.x)
+            for (int64_t w = w_lo + threadIdx.x; w < W; w += blockDim.x) a.A[(r + p) * a.ld + w] = a.B[p * a.ldb + w];
+    }
     // PLE: staged rows get their left part (old L bits, new L bits, stripe)
     if (a.mode == UPD_PLE) {
         for (int k = blockIdx.x; k < nS; k += gridDim.x) {
@@ -121,13 +137,14 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
             for (int k = 0; k < RPT; ++k) {
                 const int64_t off = rb + (int64_t)k * SLOTS + rs;
                 ri[k] = (off < nrows) ? row_lo + rr0 + off : -1;
+                if (ri[k] >= r && ri[k] < r + rbar_m) ri[k] = -1;   // M4RI pivot positions
                 src[k] = nullptr;
                 ix[k] = 0;
                 if (ri[k] >= 0) {
                     const int64_t i = ri[k];
                     ix[k] = a.idx[i * a.idx_stride];
                     const uint64_t *sp = a.A + i * a.ld;
-                    if (a.mode == UPD_PLE && i - r <= maxpos) {
+                    if ((a.mode == UPD_PLE || a.mode == UPD_M4RI) && i >= r && i - r <= maxpos) {
                         const int mv = a.map[i];
                         if (mv >= 0 && (mv >> 8) == a.stripe) sp = a.S + (int64_t)(mv & 255) * a.ldS;
                     }
@@ -205,7 +222,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     int64_t row_lo, row_hi, w_lo;
     const int64_t W = a.W;
     int64_t r = 0;
-    int maxpos = -1, nS = 0;
+    int maxpos = -1, nS = 0, rbar_m = 0;
     const StripeDesc *d = a.desc;
     if (a.mode == UPD_PLE) {
         const int rbar = d->rbar;
@@ -227,6 +244,17 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
         if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
         __syncthreads();
         if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;
+    } else if (a.mode == UPD_M4RI) {
+        rbar_m = d->rbar;
+        if (rbar_m == 0) return;
+        r = d->r;
+        row_lo = 0;
+        row_hi = a.m;
+        w_lo = d->c >> 6;
+        maxpos = d->maxpos;
+        if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
+        __syncthreads();
+        if (threadIdx.x < rbar_m) sGen[d->qbar[threadIdx.x]] = a.B + threadIdx.x * a.ldb;
     } else {
         row_lo = a.row_lo;
         row_hi = a.row_hi;
@@ -236,6 +264,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     }
     __syncthreads();
 
+    if (a.mode == UPD_M4RI) {
+        for (int p = blockIdx.x; p < rbar_m; p += gridDim.x)
+            for (int64_t w = w_lo + threadIdx.x; w < W; w += blockDim.x) a.A[(r + p) * a.ld + w] = a.B[p * a.ldb + w];
+    }
     if (a.mode == UPD_PLE && a.left_copies) {
         for (int k = blockIdx.x; k < nS; k += gridDim.x) {
             const uint64_t *src = a.S + (int64_t)k * a.ldS;
@@ -295,6 +327,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
             for (int k = 0; k < PIPE_RPT; ++k) {
                 const int64_t off = base + k * SLOTS + rs;
                 bt.ri[k] = (off < nrows) ? row0 + off : -1;
+                if (bt.ri[k] >= r && bt.ri[k] < r + rbar_m) bt.ri[k] = -1;   // M4RI pivot positions
                 bt.x0[k] = 0;
                 bt.x1[k] = 0;
                 bt.ix[k] = 0;
@@ -302,7 +335,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
                     const int64_t i = bt.ri[k];
                     bt.ix[k] = __ldg(a.idx + i * a.idx_stride);
                     const uint64_t *sp = a.A + i * a.ld;
-                    if (a.mode == UPD_PLE && i - r <= maxpos) {
+                    if ((a.mode == UPD_PLE || a.mode == UPD_M4RI) && i >= r && i - r <= maxpos) {
                         const int mv = a.map[i];
                         if (mv >= 0 && (mv >> 8) == a.stripe) sp = a.S + (int64_t)(mv & 255) * a.ldS;
                     }
@@ -371,6 +404,12 @@ cudaError_t setup_update_kernel()
     return setup_update_tma_kernel();
 }
 
+bool update_vectorised(const UpdArgs &a)
+{
+    return (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
+           ((a.mode != UPD_PLE && a.mode != UPD_M4RI) || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
+}
+
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
 {
     const size_t smem = TAB_WORDS * sizeof(uint64_t);
@@ -378,7 +417,7 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
     // and 16-byte aligned bases (staged rows too, for the PLE update), and
     // 8-byte aligned index words.
     const bool vec = (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
-                     (a.mode != UPD_PLE || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
+                     ((a.mode != UPD_PLE && a.mode != UPD_M4RI) || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
     int grid = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
     if (vec) {
         grid &= ~1;

@@ -331,10 +331,5 @@ bool encode_row_tiles(TensorMap2D *out, const uint64_t *A, int64_t m, int64_t W,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool update_vectorised(const UpdArgs &a)
-{
-    return (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
-           (a.mode != UPD_PLE || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
-}
 
 }  // namespace gf2

@@ -43,7 +43,8 @@ constexpr size_t OFF_S = al256(OFF_MAP + (size_t)NA_MAX_ROWS * 4);
 constexpr size_t OFF_GVAL = al256(OFF_S + (size_t)SMAX * NA_LDS * 8);
 constexpr size_t OFF_GLB = al256(OFF_GVAL + (size_t)NA_MAX_ROWS * 8);
 constexpr size_t OFF_GSRC = al256(OFF_GLB + (size_t)NA_MAX_ROWS * 8);
-constexpr size_t NA_BYTES = al256(OFF_GSRC + (size_t)NA_MAX_ROWS * 4);
+constexpr size_t OFF_GPOS = al256(OFF_GSRC + (size_t)NA_MAX_ROWS * 4);
+constexpr size_t NA_BYTES = al256(OFF_GPOS + (size_t)NA_MAX_ROWS * 4);
 
 }  // namespace
 
@@ -124,7 +125,7 @@ extern "C" int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_wor
     int32_t *map = reinterpret_cast<int32_t *>(base + OFF_MAP);
     uint64_t *S = reinterpret_cast<uint64_t *>(base + OFF_S);
     PanelScratch gs{reinterpret_cast<uint64_t *>(base + OFF_GVAL), reinterpret_cast<uint64_t *>(base + OFF_GLB),
-                    reinterpret_cast<int32_t *>(base + OFF_GSRC)};
+                    reinterpret_cast<int32_t *>(base + OFF_GSRC), reinterpret_cast<int32_t *>(base + OFF_GPOS)};
 
     // what must start from a known state: error flag and counters (the rank
     // and the row map are reset by the init kernel)

@@ -38,6 +38,11 @@ struct PanelShared {
     int64_t Ssrc[SMAX];        //              physical source rows
     int fail, rbar, nS, maxpos, best;
     unsigned long long colmask;
+    // block-wide path: compaction counts, and the rows with a zero stripe
+    // word that swaps moved (current position offset, source offset)
+    int cnt, nz;
+    int wcnt[32];
+    int32_t zpos[KS], zsrc[KS];
 };
 
 // Fast path, called by one whole warp: a bit-sliced window of up to 128 rows
@@ -163,79 +168,159 @@ __device__ __forceinline__ void panel_window(const uint64_t *__restrict__ A, int
         if (lane == 0) { sh.fail = fail ? 1 : 0; sh.rbar = p; }
     }
 
-// Block-wide path over all remaining rows (every thread of the block calls
-// it): eager elimination of the stripe words in the global scratch gs.
+// Block-wide path (every thread of the block): Algorithm 1's search over all
+// remaining rows.  Rows whose stripe word is zero can never hold a pivot and
+// are never changed by the stripe's eliminations, so only the nonzero rows
+// are gathered (a stable, position-ordered compaction into the scratch) and
+// searched; a zero row matters only when a swap moves it, and the few such
+// moves are tracked in shared memory.  Sparse stripes (the regime of Section
+// 4's Figure) thus cost time in proportion to their nonzero rows.  Columns
+// that are zero in every remaining row are skipped outright.
 __device__ __forceinline__ void panel_block(const uint64_t *__restrict__ A, int64_t r, int64_t ld,
                                             int64_t cw, int64_t rows, int keff, PanelScratch gs,
                                             PanelShared &sh, int32_t *fallbacks)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
-        const int nthr = blockDim.x;
-        if (tid == 0) { sh.colmask = 0; if (fallbacks) atomicAdd(fallbacks, 1); }
-        __syncthreads();
-        unsigned long long orv = 0;
-        for (int64_t sl = tid; sl < rows; sl += nthr) {
-            const uint64_t v = A[(r + sl) * ld + cw];
-            gs.val[sl] = v;
-            gs.lb[sl] = 0;
-            gs.src[sl] = (int32_t)sl;
-            orv |= v;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x;
+    if (tid == 0) {
+        sh.colmask = 0;
+        sh.cnt = 0;
+        sh.nz = 0;
+        if (fallbacks) atomicAdd(fallbacks, 1);
+    }
+    __syncthreads();
+    // 1. stable compaction of the rows with a nonzero stripe word: each
+    // thread counts a contiguous chunk of rows, a block-wide exclusive scan of
+    // the counts gives every chunk its output offset, a second pass writes
+    unsigned long long orv = 0;
+    const int64_t chunk = (rows + nthr - 1) / nthr;
+    const int64_t c0 = min(rows, (int64_t)tid * chunk), c1 = min(rows, c0 + chunk);
+    int mine = 0;
+    for (int64_t sl = c0; sl < c1; ++sl) {
+        const uint64_t v = A[(r + sl) * ld + cw];
+        orv |= v;
+        mine += (v != 0ull);
+    }
+    int incl = mine;                              // inclusive scan inside the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) sh.wcnt[warp] = incl;
+    __syncthreads();
+    int off = incl - mine;
+    for (int w2 = 0; w2 < warp; ++w2) off += sh.wcnt[w2];
+    if (tid == nthr - 1) sh.cnt = off + mine;
+    for (int64_t sl = c0; sl < c1; ++sl) {
+        const uint64_t v = A[(r + sl) * ld + cw];
+        if (v != 0ull) {
+            gs.val[off] = v;
+            gs.lb[off] = 0;
+            gs.src[off] = (int32_t)sl;
+            gs.pos[off] = (int32_t)sl;
+            ++off;
         }
-        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)orv);
-        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(orv >> 32));
-        if (lane == 0) atomicOr(&sh.colmask, ((unsigned long long)hi << 32) | lo);
+    }
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)orv);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(orv >> 32));
+    if (lane == 0) atomicOr(&sh.colmask, ((unsigned long long)hi << 32) | lo);
+    __syncthreads();
+    const uint64_t colmask = sh.colmask;
+    const int K = sh.cnt;
+    // 2. column-wise search and eager elimination over the gathered rows
+    int p = 0, first = 0;                         // pivots so far; first entry not yet retired
+    for (int j = 0; j < keff && first < K; ++j) {
+        if (!((colmask >> j) & 1ull)) continue;
+        if (tid == 0) sh.best = INT_MAX;
         __syncthreads();
-        // a column that is zero in every remaining row stays zero in every
-        // combination of them, so it can never hold a pivot
-        const uint64_t colmask = sh.colmask;
-        int p = 0, tmax = -1;
-        for (int j = 0; j < keff && p < rows; ++j) {
-            if (!((colmask >> j) & 1ull)) continue;
-            __syncthreads();
-            if (tid == 0) sh.best = INT_MAX;
-            __syncthreads();
-            for (int64_t base = p; base < rows; base += nthr) {
-                const int64_t sl = base + tid;
-                const bool hit = sl < rows && ((gs.val[sl] >> j) & 1ull);
-                if (__syncthreads_or(hit)) {
-                    if (hit) atomicMin(&sh.best, (int)sl);
-                    __syncthreads();
-                    break;
+        for (int base = first; base < K; base += nthr) {
+            const int k = base + tid;
+            const bool hit = k < K && gs.pos[k] >= 0 && ((gs.val[k] >> j) & 1ull);
+            if (__syncthreads_or(hit)) {
+                if (hit) atomicMin(&sh.best, k);
+                __syncthreads();
+                break;
+            }
+        }
+        const int kt = sh.best;
+        __syncthreads();                              // everyone has kt before sh.best is reused
+        if (kt == INT_MAX) continue;
+        if (tid == 0) {
+            // the pivot row (entry kt, at position t) swaps with the row at
+            // position p: entry `first` if it sits there, else a zero row
+            const int t = gs.pos[kt];
+            const uint64_t tv = gs.val[kt], tl = gs.lb[kt];
+            const int32_t ts = gs.src[kt];
+            sh.t[p] = t;
+            sh.j[p] = (uint8_t)j;
+            sh.E[p] = tv;
+            sh.L[p] = tl;
+            sh.Soff[p] = p;
+            sh.Ssrc[p] = r + ts;
+            if (gs.pos[first] == p) {
+                // first (the row at p) takes the pivot's place at t; the pivot retires
+                if (kt != first) {
+                    gs.val[kt] = gs.val[first];
+                    gs.lb[kt] = gs.lb[first];
+                    gs.src[kt] = gs.src[first];
                 }
+                gs.pos[first] = -1;
+            } else {
+                // a zero row sits at p: it moves to t
+                int z = -1;
+                for (int q = 0; q < sh.nz; ++q)
+                    if (sh.zpos[q] == p) z = q;
+                if (z < 0) {
+                    z = sh.nz++;
+                    sh.zsrc[z] = p;
+                }
+                sh.zpos[z] = t;
+                gs.pos[kt] = -1;
             }
-            const int t = sh.best;
-            if (t == INT_MAX) continue;
-            __syncthreads();
-            if (tid == 0) {
-                const uint64_t tv = gs.val[t], tl = gs.lb[t];
-                const int32_t ts = gs.src[t];
-                gs.val[t] = gs.val[p]; gs.lb[t] = gs.lb[p]; gs.src[t] = gs.src[p];
-                gs.val[p] = tv; gs.lb[p] = tl; gs.src[p] = ts;
-                sh.t[p] = t; sh.j[p] = (uint8_t)j; sh.E[p] = tv; sh.L[p] = tl;
-            }
-            __syncthreads();
-            const uint64_t pv = sh.E[p];
-            const uint64_t bitp = 1ull << p;
-            for (int64_t sl = p + 1 + tid; sl < rows; sl += nthr) {
-                const uint64_t v = gs.val[sl];
-                if ((v >> j) & 1ull) { gs.val[sl] = v ^ pv; gs.lb[sl] |= bitp; }
-            }
-            tmax = max(tmax, t);
-            ++p;
+            int f = first;
+            while (f < K && gs.pos[f] < 0) ++f;
+            sh.best = f;                              // the new first live entry
         }
         __syncthreads();
-        if (tid == 0) { sh.rbar = p; sh.nS = p; sh.maxpos = max(p - 1, tmax); }
-        for (int k = tid; k < p; k += nthr) { sh.Soff[k] = k; sh.Ssrc[k] = r + gs.src[k]; }
-        __syncthreads();
-        for (int64_t sl = p + tid; sl <= tmax; sl += nthr) {
-            if (gs.src[sl] != (int32_t)sl) {
-                const int k = atomicAdd(&sh.nS, 1);
-                sh.Soff[k] = (int32_t)sl;
-                sh.Ssrc[k] = r + gs.src[sl];
+        first = sh.best;
+        const uint64_t pv = sh.E[p];
+        const uint64_t bitp = 1ull << p;
+        for (int k = first + tid; k < K; k += nthr) {
+            const uint64_t v = gs.val[k];
+            if (gs.pos[k] >= 0 && ((v >> j) & 1ull)) {
+                gs.val[k] = v ^ pv;
+                gs.lb[k] |= bitp;
             }
         }
+        ++p;
         __syncthreads();
     }
+    // 3. staged rows: the pivots, then every row a swap moved
+    if (tid == 0) sh.nS = p;
+    __syncthreads();
+    for (int k = first + tid; k < K; k += nthr) {
+        const int32_t ps = gs.pos[k];
+        if (ps >= 0 && ps != gs.src[k]) {
+            const int q = atomicAdd(&sh.nS, 1);
+            sh.Soff[q] = ps;
+            sh.Ssrc[q] = r + gs.src[k];
+        }
+    }
+    if (tid < sh.nz && sh.zpos[tid] != sh.zsrc[tid]) {
+        const int q = atomicAdd(&sh.nS, 1);
+        sh.Soff[q] = sh.zpos[tid];
+        sh.Ssrc[q] = r + sh.zsrc[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int mx = p - 1;
+        for (int q = 0; q < sh.nS; ++q) mx = max(mx, (int)sh.Soff[q]);
+        sh.rbar = p;
+        sh.maxpos = mx;
+    }
+    __syncthreads();
+}
 
 // Rows of L11^-1 (L11 unit lower triangular, rows Lrows[0..rbar)), by one
 // warp: forward substitution per column (lane owns columns lane and

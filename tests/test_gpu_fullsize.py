@@ -63,6 +63,14 @@ def ple_and_rref_checked(h, A, m, n, expect_rank=None):
     assert r2 == r
     assert np.array_equal(Q2.cpu().numpy()[: min(m, n)], Qh)
     assert oracle.check_rref(R, LE, m, n, Qh, r) == 0
+    # M4RI (Algorithm 8) reaches the same unique RREF
+    dM = to_dev(A)
+    Q3 = vec_dev(min(m, n))
+    r3 = h.rref_m4ri(dM, m, n, Q3)
+    M = to_host(dM, gi.words_for(n))
+    del dM
+    assert r3 == r and np.array_equal(Q3.cpu().numpy()[: min(m, n)], Qh)
+    assert oracle.check_rref(M, LE, m, n, Qh, r) == 0
     return r
 
 
