@@ -231,7 +231,7 @@ int gf2_rref_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_
  *   A, P, Q, rank  as gf2_ple (A, P, Q device pointers; rank a host int64*).
  *   stream         a cudaStream_t passed as void* (NULL: the default stream).
  * Limits: m <= 4096 and n <= 4096; larger sizes return GF2_EINVAL and enqueue
- * nothing.  Scratch: one fixed array of about 0.4 MiB inside the library,
+ * nothing.  Scratch: one fixed array of about 0.5 MiB inside the library,
  * held on every GPU that loads the library until the process exits.  The
  * first call on a device (with that device current) looks up the array's
  * device address; make that first call before any stream capture.  Every

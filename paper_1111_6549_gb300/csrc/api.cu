@@ -75,7 +75,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int64_t words_for(int64_t n) { return (n + 63) >> 6; }
 
 struct Layout {
-    size_t descs, idx, map, S, G, gval, glb, gsrc, P, Q, total;
+    size_t descs, idx, map, S, G, ptab, gval, glb, gsrc, P, Q, total;
     int64_t ldS;
 };
 
@@ -92,6 +92,7 @@ Layout layout_for(int64_t m, int64_t ncols)
     L.map = off;   off = align256(off + (size_t)mm * 8);   // two halves, by stripe parity
     L.S = off;     off = align256(off + (size_t)SMAX * L.ldS * 8);
     L.G = off;     off = align256(off + (size_t)KS * L.ldS * 8);     // M4RI: reduced pivot rows
+    L.ptab = off;  off = align256(off + 2 * PREP_TAB_BYTES);           // prep tables, by stripe parity
     L.gval = off;  off = align256(off + (size_t)mm * 8);
     L.glb = off;   off = align256(off + (size_t)mm * 8);
     L.gsrc = off;  off = align256(off + (size_t)mm * 8);   // source offsets, then positions
@@ -233,6 +234,9 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     // stripe's panel (running early, on the side stream) never overwrites an
     // entry the current update still reads.
     auto map_of = [&](int64_t s) { return map + (s & 1) * std::max<int64_t>(m, 1); };
+    auto ptab_of = [&](int64_t s) {
+        return reinterpret_cast<uint64_t *>(ws + L.ptab) + (s & 1) * (3 * PREP_TAB_WORDS);
+    };
     CK(cudaMemsetAsync(map, 0xFF, (size_t)std::max<int64_t>(m, 1) * 8, h->stream));
     {
         Timed t(h, K_OTHER);
@@ -241,14 +245,15 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     h->launches += 1;
     auto panel = [&](cudaStream_t st, int64_t s) -> int {
         Timed t(h, K_PANEL, st);
-        CK(launch_panel(st, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map_of(s), gs, fb_dev(h)));
+        CK(launch_panel(st, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map_of(s), gs, fb_dev(h),
+                        ptab_of(s)));
         h->launches += 1;
         return GF2_OK;
     };
     auto prep = [&](int64_t s) -> int {
         Timed t(h, K_PREP);
         CK(launch_prep(h->stream, A, m, ld, W, (int)s, descs, map_of(s), S, L.ldS, IDX, err_dev(h),
-                       h->num_sms));
+                       ptab_of(s), h->num_sms));
         h->launches += 1;
         return GF2_OK;
     };
@@ -383,7 +388,7 @@ int run_m4ri(gf2_handle *h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64
     for (int64_t s = 0; s < W; ++s) {
         {
             Timed t(h, K_PANEL);
-            CK(launch_panel(h->stream, A, m, ld, n, (int)s, descs, r_dev(h), P, Q, map, gs, fb_dev(h)));
+            CK(launch_panel(h->stream, A, m, ld, n, (int)s, descs, r_dev(h), P, Q, map, gs, fb_dev(h), nullptr));
         }
         {
             Timed t(h, K_PREP);

@@ -119,13 +119,18 @@ bool encode_row_tiles(TensorMap2D *out, const uint64_t *A, int64_t m, int64_t W,
 // ---- launchers (host side, defined in the .cu files) ----
 cudaError_t launch_init_ple(cudaStream_t st, int64_t *P, int64_t *Q, int64_t m, int64_t qn,
                             int32_t *map, int64_t *r_dev, int num_sms);
+// The panel kernel also builds the prep kernel's lookup tables (3 x 8 x 256
+// words, PREP_TAB_BYTES) in ptab when it is not null; the PLE's prep reads them.
+constexpr int PREP_TAB_WORDS = 8 * 256;
+constexpr size_t PREP_TAB_BYTES = 3 * PREP_TAB_WORDS * sizeof(uint64_t);
 cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t npiv, int s,
                          StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
-                         PanelScratch gs, int32_t *fallbacks);
+                         PanelScratch gs, int32_t *fallbacks, uint64_t *ptab);
 cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
                         StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
-                        uint64_t *IDX, int32_t *err, int num_sms);
+                        uint64_t *IDX, int32_t *err, const uint64_t *ptab, int num_sms);
 cudaError_t setup_update_kernel();
+cudaError_t setup_prep_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
 bool update_vectorised(const UpdArgs &a);   // true when the paired, pipelined form runs
 cudaError_t launch_update_tc(cudaStream_t st, const UpdArgs &a, int num_sms);

@@ -60,7 +60,7 @@ cudaError_t launch_init_ple(cudaStream_t st, int64_t *P, int64_t *Q, int64_t m, 
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv, int s,
              StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
-             PanelScratch gs, int32_t *fallbacks)
+             PanelScratch gs, int32_t *fallbacks, uint64_t *ptab)
 {
     __shared__ PanelShared sh;
     StripeDesc *d = descs + s;
@@ -126,14 +126,55 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         d->tier = sh.fail ? 2 : 1;
         *r_dev = r + rbar;
     }
+    if (ptab == nullptr) return;
+    // The prep kernel's tables (three x eight x 256 words): for a stripe word
+    // with bits u on the pivot columns, the L coefficients v = u U11^-1, the
+    // table index v L11^-1 and the word rebuilt from the pivot bits
+    // (u U11^-1 E11) are XORs of rows selected by u, looked up per raw byte
+    // of the word (non-pivot columns select nothing).
+    __shared__ uint64_t tMv[KS], tMx[KS], tMg[KS];
+    __shared__ int8_t tcolp[KS];
+    __syncthreads();                                   // Minv and Linv are written
+    if (tid < KS) tcolp[tid] = -1;
+    __syncthreads();
+    if (tid < rbar) {
+        const uint64_t mp = d->Minv[tid];
+        uint64_t x = 0, g = 0;
+        for (int q = 0; q < rbar; ++q)
+            if ((mp >> q) & 1ull) {
+                x ^= d->Linv[q];
+                g ^= sh.E[q];
+            }
+        tMv[tid] = mp;
+        tMx[tid] = x;
+        tMg[tid] = g;
+        tcolp[sh.j[tid]] = (int8_t)tid;
+    }
+    __syncthreads();
+    for (int e2 = tid; e2 < 8 * 256; e2 += blockDim.x) {
+        const int b = e2 >> 8, e = e2 & 255;
+        uint64_t av = 0, ax = 0, ag = 0;
+#pragma unroll
+        for (int bq = 0; bq < 8; ++bq) {
+            const int p = tcolp[8 * b + bq];
+            if (((e >> bq) & 1) && p >= 0) {
+                av ^= tMv[p];
+                ax ^= tMx[p];
+                ag ^= tMg[p];
+            }
+        }
+        ptab[e2] = av;
+        ptab[PREP_TAB_WORDS + e2] = ax;
+        ptab[2 * PREP_TAB_WORDS + e2] = ag;
+    }
 }
 
 cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t npiv, int s,
                          StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
-                         PanelScratch gs, int32_t *fallbacks)
+                         PanelScratch gs, int32_t *fallbacks, uint64_t *ptab)
 {
     panel_kernel<<<1, PANEL_THREADS, 0, st>>>(A, m, ld, npiv, s, descs, r_dev, P, Q, map, gs,
-                                              fallbacks);
+                                              fallbacks, ptab);
     return cudaGetLastError();
 }
 
@@ -164,7 +205,8 @@ constexpr int PREP_FIRST_ROW_BLOCK = PREP_STAGE_BLOCKS;
 
 __global__ void __launch_bounds__(PREP_THREADS)
 prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *descs,
-            const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *IDX, int32_t *err)
+            const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *IDX, int32_t *err,
+            const uint64_t *__restrict__ ptab)
 {
     StripeDesc *d = descs + s;
     const int rbar = d->rbar;
@@ -174,11 +216,9 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
     const int nS = d->nS;
     const int maxpos = d->maxpos;
     __shared__ uint64_t sE[KS], sLinv[KS];
-    __shared__ int sq[KS];
     for (int i = threadIdx.x; i < rbar; i += blockDim.x) {
         sE[i] = d->E11[i];
         sLinv[i] = d->Linv[i];
-        sq[i] = d->qbar[i];
     }
     __syncthreads();
 
@@ -197,17 +237,20 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
                     es = sE[k];
                     ix = sLinv[k] ^ (1ull << k);
                 } else {
-                    uint64_t sw = dst[cw];
+                    // a displaced row: the same table lookups as every other row
+                    const uint64_t sw = dst[cw];
+                    uint64_t g = 0;
                     v = 0;
-                    for (int p = 0; p < rbar; ++p) {
-                        const uint64_t bit = (sw >> sq[p]) & 1ull;
-                        sw ^= sE[p] & (0ull - bit);
-                        v |= bit << p;
-                    }
-                    if (sw && err) atomicExch(err, 1);
-                    es = 0;
                     ix = 0;
-                    for (int p = 0; p < rbar; ++p) ix ^= sLinv[p] & (0ull - ((v >> p) & 1ull));
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        const int e = (int)((sw >> (8 * b)) & 255ull) + 256 * b;
+                        v ^= __ldg(ptab + e);
+                        ix ^= __ldg(ptab + PREP_TAB_WORDS + e);
+                        g ^= __ldg(ptab + 2 * PREP_TAB_WORDS + e);
+                    }
+                    if (g != sw && err) atomicExch(err, 1);
+                    es = 0;
                 }
                 write_lregion(dst, r, cw, rbar, v, es);
                 IDX[pos] = ix;
@@ -216,6 +259,12 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
         }
         return;
     }
+    // Every other row at a position >= r: its L coefficients v = u U11^-1
+    // (u = its bits on the pivot columns), its table index v L11^-1, and the
+    // stripe word rebuilt from u, each as eight lookups by the raw bytes of the
+    // stripe word in the tables the panel kernel built (read through L1).  A
+    // row whose word is not rebuilt exactly lies outside the span of E11: an
+    // internal error.
     const int64_t stride = (int64_t)(gridDim.x - PREP_FIRST_ROW_BLOCK) * blockDim.x;
     for (int64_t i = r + (int64_t)(blockIdx.x - PREP_FIRST_ROW_BLOCK) * blockDim.x + threadIdx.x;
          i < m; i += stride) {
@@ -224,30 +273,32 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
             if (mv >= 0 && (mv >> 8) == s) continue;       // staged row
         }
         uint64_t *row = A + i * ld;
-        uint64_t sw = row[cw];
-        uint64_t v = 0;
-        for (int p = 0; p < rbar; ++p) {
-            const uint64_t bit = (sw >> sq[p]) & 1ull;
-            sw ^= sE[p] & (0ull - bit);
-            v |= bit << p;
+        const uint64_t sw = row[cw];
+        uint64_t v = 0, ix = 0, g = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int e = (int)((sw >> (8 * b)) & 255ull) + 256 * b;
+            v ^= __ldg(ptab + e);
+            ix ^= __ldg(ptab + PREP_TAB_WORDS + e);
+            g ^= __ldg(ptab + 2 * PREP_TAB_WORDS + e);
         }
-        if (sw && err) atomicExch(err, 1);
-        uint64_t ix = 0;
-        for (int p = 0; p < rbar; ++p) ix ^= sLinv[p] & (0ull - ((v >> p) & 1ull));
+        if (g != sw && err) atomicExch(err, 1);
         write_lregion(row, r, cw, rbar, v, 0ull);
         IDX[i] = ix;
     }
 }
 
+cudaError_t setup_prep_kernel() { return cudaSuccess; }
+
 cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
                         StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
-                        uint64_t *IDX, int32_t *err, int num_sms)
+                        uint64_t *IDX, int32_t *err, const uint64_t *ptab, int num_sms)
 {
     int64_t blocks = (m + PREP_THREADS - 1) / PREP_THREADS;
     if (blocks < 1) blocks = 1;
     if (blocks > 4 * num_sms) blocks = 4 * num_sms;
     prep_kernel<<<(int)(blocks + PREP_FIRST_ROW_BLOCK), PREP_THREADS, 0, st>>>(
-        A, m, ld, W, s, descs, map, S, ldS, IDX, err);
+        A, m, ld, W, s, descs, map, S, ldS, IDX, err, ptab);
     return cudaGetLastError();
 }
 

@@ -401,7 +401,9 @@ cudaError_t setup_update_kernel()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(update_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return setup_update_tma_kernel();
+    e = setup_update_tma_kernel();
+    if (e != cudaSuccess) return e;
+    return setup_prep_kernel();   // the prep kernel's 48 KiB of tables
 }
 
 bool update_vectorised(const UpdArgs &a)

@@ -10,7 +10,7 @@
 // need taken from one fixed array that is part of the library image.
 //
 // The scratch is the file-scope __device__ array below.  Every GPU that loads
-// the library holds it (NA_BYTES, about 0.4 MiB) until the process exits.  In
+// the library holds it (NA_BYTES, about 0.5 MiB) until the process exits.  In
 // host code the array's name is only a host-side stand-in, so the address the
 // kernels get comes from cudaGetSymbolAddress, looked up once per device (on
 // the first call made with that device current) and cached.
@@ -44,7 +44,8 @@ constexpr size_t OFF_GVAL = al256(OFF_S + (size_t)SMAX * NA_LDS * 8);
 constexpr size_t OFF_GLB = al256(OFF_GVAL + (size_t)NA_MAX_ROWS * 8);
 constexpr size_t OFF_GSRC = al256(OFF_GLB + (size_t)NA_MAX_ROWS * 8);
 constexpr size_t OFF_GPOS = al256(OFF_GSRC + (size_t)NA_MAX_ROWS * 4);
-constexpr size_t NA_BYTES = al256(OFF_GPOS + (size_t)NA_MAX_ROWS * 4);
+constexpr size_t OFF_PTAB = al256(OFF_GPOS + (size_t)NA_MAX_ROWS * 4);
+constexpr size_t NA_BYTES = al256(OFF_PTAB + PREP_TAB_BYTES);
 
 }  // namespace
 
@@ -133,8 +134,9 @@ extern "C" int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_wor
     NA_CK(launch_init_ple(st, P, Q, m, n > 0 ? (m < n ? m : n) : 0, map, r_dev, nd->num_sms));
     const int64_t ns = W;
     for (int64_t s = 0; s < ns; ++s) {
-        NA_CK(launch_panel(st, A, m, ld_words, n, (int)s, descs, r_dev, P, Q, map, gs, fallbacks));
-        NA_CK(launch_prep(st, A, m, ld_words, W, (int)s, descs, map, S, NA_LDS, IDX, err, nd->num_sms));
+        uint64_t *ptab = reinterpret_cast<uint64_t *>(base + OFF_PTAB);
+        NA_CK(launch_panel(st, A, m, ld_words, n, (int)s, descs, r_dev, P, Q, map, gs, fallbacks, ptab));
+        NA_CK(launch_prep(st, A, m, ld_words, W, (int)s, descs, map, S, NA_LDS, IDX, err, ptab, nd->num_sms));
         UpdArgs a{};
         a.tp_lo = 0;
         a.tp_hi = -1;
