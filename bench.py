@@ -413,20 +413,23 @@ def tc_compare(args):
         return statistics.median(ts)
 
     out = {"mode": "tc_compare", "mul": [], "ple": []}
-    for (m, k, n) in [(16384, 64, 16384), (16384, 1024, 16384), (16384, 16384, 16384)]:
+    for (m, k, n) in [(16384, 64, 16384), (16384, 1024, 16384), (16384, 2048, 16384), (16384, 4096, 16384),
+                      (16384, 16384, 16384), (32768, 32768, 32768)]:
         A = torch.from_numpy(gi.bernoulli_matrix(m, k, 1).view(np.int64)).to(dev)
         B = torch.from_numpy(gi.bernoulli_matrix(k, n, 2).view(np.int64)).to(dev)
         C = torch.zeros((m, gi.words_for(n)), dtype=torch.int64, device=dev)
         res, outs = {"m": m, "k": k, "n": n}, {}
-        for tc in (0, 1):
+        for name, tc, gk in (("table", 0, 0), ("tcgen05", 1, 0), ("fp8_gemm", 0, 1)):
             h.set_option(g.OPT_TC_MUL, tc)
-            res["tc_ms" if tc else "table_ms"] = timeit(lambda: h.mul(C, A, B, m, k, n))
-            outs[tc] = C.clone()
-        res["identical"] = bool(torch.equal(outs[0], outs[1]))
-        res["tc_tera_and_xor_per_s"] = m * k * n / (res["tc_ms"] / 1e3) / 1e12
-        res["table_tera_and_xor_per_s"] = m * k * n / (res["table_ms"] / 1e3) / 1e12
+            h.set_option(g.OPT_MUL_GEMM_MIN_K, gk)
+            res[name + "_ms"] = timeit(lambda: h.mul(C, A, B, m, k, n))
+            res[name + "_tera_and_xor_per_s"] = m * k * n / (res[name + "_ms"] / 1e3) / 1e12
+            outs[name] = C.clone()
+        res["identical"] = bool(torch.equal(outs["table"], outs["tcgen05"]) and
+                                torch.equal(outs["table"], outs["fp8_gemm"]))
         out["mul"].append(res)
     h.set_option(g.OPT_TC_MUL, 0)
+    h.set_option(g.OPT_MUL_GEMM_MIN_K, 4096)
     for nn in (16384, 32768):
         A = torch.from_numpy(gi.dense_square(nn).view(np.int64)).to(dev)
         Wk = torch.empty_like(A)
@@ -465,6 +468,8 @@ def run_ours(args):
     h = g.Handle(local)
     if args.tma:
         h.set_option(g.OPT_TMA_UPDATE, 1)
+    if args.ple_block is not None:
+        h.set_option(g.OPT_PLE_BLOCK, args.ple_block)
     stream = torch.cuda.current_stream(dev)
 
     m = n = args.n
@@ -707,6 +712,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--ple-block", type=int, default=None,
+                    help="PLE column block for the blocked trailing update (GF2_OPT_PLE_BLOCK)")
     ap.add_argument("--tma", action="store_true",
                     help="run the update in its TMA-staged form (GF2_OPT_TMA_UPDATE)")
     ap.add_argument("--tc-compare", action="store_true",

@@ -297,15 +297,33 @@ int gf2_server_destroy(gf2_server_t server);
  *                      shared memory by TMA (a producer warp, five stages)
  *                      where the matrix allows it (16-byte aligned base, even
  *                      ld_words, at least 16 words and 256 rows)
- * Look-ahead is on by default; the tensor-core and TMA forms are off (the
+ *   GF2_OPT_MUL_GEMM_MIN_K  gf2_mul with an inner dimension k >= value (0:
+ *                      never) runs as an exact FP8 GEMM: the library's own
+ *                      kernels expand the bits to FP8 0/1, a plain cuBLASLt
+ *                      FP8 GEMM counts, and the library takes the parities;
+ *                      below it, the Four-Russians tables (default 4096)
+ *   GF2_OPT_PLE_BLOCK  value > 0 (a multiple of 64): PLE (and everything
+ *                      built on it) decomposes value columns at a time with
+ *                      the updates inside the block, then applies the
+ *                      block's trailing update at once -- the row moves, the
+ *                      TRSM U = L11^-1 A12 and the product A22 ^= L21 U
+ *                      through gf2_mul (Algorithm 3's A11 += A10 A01 step);
+ *                      the host then reads the rank once per block, so the
+ *                      _async calls wait for each block's pivot search;
+ *                      0: one table update per 64-column stripe; -1
+ *                      (default): blocks of half the pivot columns from
+ *                      65536 pivot columns on, else 0
+ * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
- * GF2_EINVAL for an unknown option.
+ * GF2_EINVAL for an unknown option or a negative value.
  */
-#define GF2_OPT_LOOKAHEAD  1
-#define GF2_OPT_TC_MUL     2
-#define GF2_OPT_TC_UPDATE  3
-#define GF2_OPT_TMA_UPDATE 4
+#define GF2_OPT_LOOKAHEAD       1
+#define GF2_OPT_TC_MUL          2
+#define GF2_OPT_TC_UPDATE       3
+#define GF2_OPT_TMA_UPDATE      4
+#define GF2_OPT_MUL_GEMM_MIN_K  5
+#define GF2_OPT_PLE_BLOCK       6
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */

@@ -59,7 +59,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 1)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublasLt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

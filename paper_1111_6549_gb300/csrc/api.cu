@@ -45,6 +45,13 @@ struct gf2_handle {
     double kind_ms[5] = {0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other
     BatchTune btune{};             // batched kernel: table configuration per size class
     bool tma = false;              // update rows move by TMA where A allows it (measured slower)
+    int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the FP8 GEMM
+    int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
+    char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
+    size_t lbuf_cap = 0;
+    void *lt = nullptr;            // cuBLASLt state (created on first use)
+    char *gbuf = nullptr;          // FP8 operands and fp32 counts of the GEMM path
+    size_t gbuf_cap = 0;
     TensorMap2D tmap{};            // TMA descriptor of the last updated matrix
     const void *tm_A = nullptr;
     int64_t tm_m = -1, tm_W = -1, tm_ld = -1;
@@ -211,10 +218,13 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
     return GF2_OK;
 }
 
-// Enqueue the block-iterative PLE of A (m x ncols, pivots among the first
-// npiv columns).  The rank is left in r_dev.
-int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv,
-            int64_t *P, int64_t *Q)
+// Enqueue stripes [s_lo, s_hi) of the block-iterative PLE of A (m x ncols,
+// pivots among the first npiv columns), updating the words [.., W_upd) of
+// every row (the words from W_upd on move with their rows but are otherwise
+// left alone).  init: start from rank 0 (P, Q, row map reset).  The rank is
+// left in r_dev.
+int run_ple_range(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv, int64_t *P,
+                  int64_t *Q, int64_t s_lo, int64_t s_hi, int64_t W_upd, bool init, bool move_rest = true)
 {
     const Layout L = layout_for(m, ncols);
     int rc = grow(&h->ws, &h->ws_cap, L.total, h->stream);
@@ -229,7 +239,6 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
                     reinterpret_cast<int32_t *>(ws + L.gsrc) + std::max<int64_t>(m, 1)};
     const int64_t qn = std::min(m, npiv);
     const int64_t W = words_for(ncols);
-    const int64_t ns = words_for(npiv);
     // The row map has two halves: stripe s uses half s & 1, so the next
     // stripe's panel (running early, on the side stream) never overwrites an
     // entry the current update still reads.
@@ -237,12 +246,14 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     auto ptab_of = [&](int64_t s) {
         return reinterpret_cast<uint64_t *>(ws + L.ptab) + (s & 1) * (3 * PREP_TAB_WORDS);
     };
-    CK(cudaMemsetAsync(map, 0xFF, (size_t)std::max<int64_t>(m, 1) * 8, h->stream));
-    {
-        Timed t(h, K_OTHER);
-        CK(launch_init_ple(h->stream, P, Q, m, qn, nullptr, r_dev(h), h->num_sms));
+    if (init) {
+        CK(cudaMemsetAsync(map, 0xFF, (size_t)std::max<int64_t>(m, 1) * 8, h->stream));
+        {
+            Timed t(h, K_OTHER);
+            CK(launch_init_ple(h->stream, P, Q, m, qn, nullptr, r_dev(h), h->num_sms));
+        }
+        h->launches += 1;
     }
-    h->launches += 1;
     auto panel = [&](cudaStream_t st, int64_t s) -> int {
         Timed t(h, K_PANEL, st);
         CK(launch_panel(st, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map_of(s), gs, fb_dev(h),
@@ -263,7 +274,8 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
         a.A = A;
         a.ld = ld;
         a.m = m;
-        a.W = W;
+        a.W = W_upd;
+        a.W_full = move_rest ? W : 0;
         a.desc = descs + s;
         a.stripe = (int)s;
         a.S = S;
@@ -284,10 +296,10 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     probe.ld = ld;
     probe.S = S;
     probe.ldS = L.ldS;
-    const bool la = h->lookahead && !h->tc_update && h->side && ns > 1 && update_vectorised(probe) &&
+    const bool la = h->lookahead && !h->tc_update && h->side && s_hi - s_lo > 1 && update_vectorised(probe) &&
                     h->num_sms >= 8;
     if (!la) {
-        for (int64_t s = 0; s < ns; ++s) {
+        for (int64_t s = s_lo; s < s_hi; ++s) {
             if ((rc = panel(h->stream, s))) return rc;
             if ((rc = prep(s))) return rc;
             if ((rc = upd(s, 0, -1, 1, 0))) return rc;
@@ -300,10 +312,10 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     // but two SMs; prep(s+1) waits for both.
     CK(cudaEventRecord(h->ev_fork, h->stream));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-    if ((rc = panel(h->stream, 0))) return rc;
-    if ((rc = prep(0))) return rc;
-    for (int64_t s = 0; s < ns; ++s) {
-        if (s + 1 < ns) {
+    if ((rc = panel(h->stream, s_lo))) return rc;
+    if ((rc = prep(s_lo))) return rc;
+    for (int64_t s = s_lo; s < s_hi; ++s) {
+        if (s + 1 < s_hi) {
             if ((rc = upd(s, 0, 1, 1, 0))) return rc;
             CK(cudaEventRecord(h->ev_u1, h->stream));
             CK(cudaStreamWaitEvent(h->side, h->ev_u1, 0));
@@ -315,6 +327,120 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
         } else {
             if ((rc = upd(s, 0, -1, 1, 0))) return rc;
         }
+    }
+    return GF2_OK;
+}
+
+// X <- L^-1 X for the kb rows X = A[row0 .. row0+kb), words [w_lo, W), with
+// L the unit lower triangular kb x kb matrix whose strictly lower bits are the
+// gathered rows Lt (kb x ldt words, aligned).  Large blocks split in halves
+// (X2 ^= L21 X1 through gf2_mul between the two half solves); from 2048 rows
+// down, 64 pivots at a time: the 64 x 64 diagonal inverse, then one table
+// pass over the rows below.
+static int trsm_lower(gf2_handle *h, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
+                      int64_t ldt, int64_t w_lo, int64_t W, int64_t ncols)
+{
+    if (kb > 2048) {
+        const int64_t hh = ((kb / 2) + 63) & ~int64_t(63);
+        int rc = trsm_lower(h, A, ld, row0, hh, Lt, ldt, w_lo, W, ncols);
+        if (rc) return rc;
+        rc = gf2_mul(h, A + (row0 + hh) * ld + w_lo, ld, Lt + hh * ldt, ldt, A + row0 * ld + w_lo, ld, kb - hh, hh,
+                     ncols - 64 * w_lo, 1);
+        if (rc) return rc;
+        return trsm_lower(h, A, ld, row0 + hh, kb - hh, Lt + hh * ldt + hh / 64, ldt, w_lo, W, ncols);
+    }
+    const int64_t kw = words_for(kb);
+    for (int64_t t = 0; t < kw; ++t) {
+        const int nt = (int)std::min<int64_t>(64, kb - 64 * t);
+        {
+            Timed tt(h, K_OTHER);
+            CK(launch_trsm_diag(h->stream, A, ld, row0 + 64 * t, nt, Lt, ldt, t, w_lo, W, h->num_sms));
+        }
+        h->launches += 1;
+        if (64 * (t + 1) < kb) {
+            UpdArgs a{};
+            a.tp_lo = 0;
+            a.tp_hi = -1;
+            a.left_copies = 1;
+            a.mode = UPD_MUL;
+            a.A = A + row0 * ld;                            // rows relative to row0
+            a.ld = ld;
+            a.m = kb;
+            a.W = W;
+            a.idx = Lt + t;
+            a.idx_stride = ldt;
+            a.B = A + (row0 + 64 * t) * ld;
+            a.ldb = ld;
+            a.gen_count = nt;
+            a.row_lo = 64 * (t + 1);
+            a.row_hi = kb;
+            a.w_lo = w_lo;
+            a.bytes = bytes_dev(h);
+            int rc = launch_update_counted(h, a);
+            if (rc) return rc;
+        }
+    }
+    return GF2_OK;
+}
+
+// Enqueue the block-iterative PLE of A (m x ncols, pivots among the first
+// npiv columns); the rank is left in r_dev.  With a PLE block width set
+// (GF2_OPT_PLE_BLOCK), the stripes are decomposed block by block with their
+// updates restricted to the block, and the columns right of each block get
+// the block's whole trailing update at once: the TRSM U = L11^-1 A12 on the
+// block's pivot rows (one 64 x 64 diagonal inverse plus one table pass per
+// 64 pivots) and A22 ^= L21 U through gf2_mul (the FP8 GEMM for large
+// blocks).  The host reads the rank once per block.
+int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv, int64_t *P,
+            int64_t *Q)
+{
+    const int64_t W = words_for(ncols), ns = words_for(npiv);
+    // stripes per block; automatic: one split in the middle from 65536 pivot
+    // columns on (measured on GB300: 65536^2 PLE 120 ms against 129 ms per
+    // stripe; at 32768^2 the per-stripe form is faster)
+    const int64_t bs = h->ple_block >= 0 ? h->ple_block / 64 : (npiv >= 65536 ? (ns + 1) / 2 : 0);
+    if (bs <= 0 || ns <= bs) return run_ple_range(h, A, m, ncols, ld, npiv, P, Q, 0, ns, W, true);
+    int64_t r0 = 0;
+    for (int64_t s0 = 0; s0 < ns; s0 += bs) {
+        const int64_t s1 = std::min(ns, s0 + bs);
+        const bool last = s1 == ns;
+        const int64_t W_upd = last ? W : s1;
+        int rc = run_ple_range(h, A, m, ncols, ld, npiv, P, Q, s0, s1, W_upd, s0 == 0, last);
+        if (rc) return rc;
+        if (last) break;
+        // the block's row moves, applied to the words right of it at once
+        {
+            Timed t(h, K_OTHER);
+            CK(launch_permute_trailing(h->stream, A, ld, reinterpret_cast<StripeDesc *>(h->ws + layout_for(m, ncols).descs),
+                                       (int)s0, (int)s1, W_upd, W));
+        }
+        h->launches += 1;
+        int64_t r1 = 0;
+        CK(cudaMemcpyAsync(&r1, r_dev(h), sizeof(r1), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const int64_t kb = r1 - r0;
+        if (kb > 0) {
+            // the block's L bits, rows r0 .. m, aligned
+            const int64_t kw = words_for(kb);
+            rc = grow(&h->lbuf, &h->lbuf_cap, (size_t)(m - r0) * kw * 8, h->stream);
+            if (rc) return rc;
+            uint64_t *Lt = reinterpret_cast<uint64_t *>(h->lbuf);
+            {
+                Timed t(h, K_OTHER);
+                CK(launch_gather_lbits(h->stream, A, ld, W, r0, m - r0, r0, kb, kw, Lt, h->num_sms));
+            }
+            h->launches += 1;
+            // U = L11^-1 A[r0:r1, W_upd:W]
+            if ((rc = trsm_lower(h, A, ld, r0, kb, Lt, kw, W_upd, W, ncols))) return rc;
+            // A[r1:m, W_upd:W] ^= L21 U
+            if (r1 < m) {
+                rc = gf2_mul(h, A + r1 * ld + W_upd, ld, Lt + kb * kw, kw, A + r0 * ld + W_upd, ld, m - r1, kb,
+                             ncols - 64 * W_upd, 1);
+                if (rc) return rc;
+            }
+        }
+        r0 = r1;
+        if (r1 >= m) break;                              // no row left to pivot on
     }
     return GF2_OK;
 }
@@ -509,6 +635,9 @@ int gf2_destroy(gf2_handle_t h)
     cudaFree(h->ws);
     cudaFree(h->io);
     cudaFree(h->bws);
+    cudaFree(h->gbuf);
+    cudaFree(h->lbuf);
+    gemm_lt_destroy(h->lt);
     cudaFree(h->small);
     delete h;
     return GF2_OK;
@@ -644,6 +773,56 @@ int gf2_rref_m4ri_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64
     return GF2_OK;
 }
 
+// C ^= A B through the FP8 GEMM (kernels_gemm.cu): B is expanded once per
+// chunk of at most 2^22 rows (fp32 counts stay exact and below 2^23), A and
+// the fp32 counts in row blocks of about 1 GiB of counts.
+static int mul_gemm(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
+                    int64_t ldb, int64_t m, int64_t k, int64_t n)
+{
+    if (!h->lt) {
+        h->lt = gemm_lt_create();
+        if (!h->lt) return GF2_ECUDA;
+    }
+    constexpr int64_t KCH = int64_t(1) << 22;
+    const int64_t ldd = (n + 15) & ~int64_t(15);
+    for (int64_t k0 = 0; k0 < k; k0 += KCH) {
+        const int64_t kc = std::min(KCH, k - k0);
+        const int64_t kp = (kc + 63) & ~int64_t(63);
+        int64_t mb = std::max<int64_t>(1, (int64_t(1) << 30) / (ldd * 4));
+        mb = std::min(mb, m);
+        mb = (mb + 15) & ~int64_t(15);
+        const size_t bbytes = align256((size_t)n * kp), abytes = align256((size_t)mb * kp),
+                     dbytes = align256((size_t)mb * ldd * 4);
+        int rc = grow(&h->gbuf, &h->gbuf_cap, bbytes + abytes + dbytes, h->stream);
+        if (rc) return rc;
+        uint8_t *B8t = reinterpret_cast<uint8_t *>(h->gbuf);
+        uint8_t *A8 = reinterpret_cast<uint8_t *>(h->gbuf + bbytes);
+        float *D = reinterpret_cast<float *>(h->gbuf + bbytes + abytes);
+        {
+            Timed t(h, K_OTHER);
+            CK(launch_expand_transpose(h->stream, B + k0 * ldb, ldb, 0, kc, n, kp, B8t, h->num_sms));
+        }
+        h->launches += 1;
+        for (int64_t i0 = 0; i0 < m; i0 += mb) {
+            const int64_t rows = std::min(mb, m - i0);
+            {
+                Timed t(h, K_OTHER);
+                CK(launch_expand_rows(h->stream, A + i0 * lda, lda, rows, k0, k0 + kc, kp, A8, h->num_sms));
+            }
+            {
+                Timed t(h, K_OTHER);
+                if (gemm_fp8_counts(h->lt, h->stream, A8, B8t, D, rows, n, kp, ldd) != 0) return GF2_ECUDA;
+            }
+            {
+                Timed t(h, K_OTHER);
+                CK(launch_parity(h->stream, D, ldd, rows, n, C + i0 * ldc, ldc, h->num_sms));
+            }
+            h->launches += 2;
+        }
+    }
+    return GF2_OK;
+}
+
 int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
             int64_t ldb, int64_t m, int64_t k, int64_t n, int accumulate)
 {
@@ -655,6 +834,7 @@ int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t
     const int64_t Wc = words_for(n);
     if (!accumulate)
         CK(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)Wc * 8, (size_t)m, h->stream));
+    if (!h->tc_mul && h->gemm_min_k > 0 && k >= h->gemm_min_k) return mul_gemm(h, C, ldc, A, lda, B, ldb, m, k, n);
     if (h->tc_mul && k > 0) {
         // tensor cores: every 64-column chunk of A accumulates into the same
         // counts in tensor memory, so C is read and written once per group of
@@ -1163,6 +1343,14 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
     case GF2_OPT_TC_MUL: h->tc_mul = value != 0; return GF2_OK;
     case GF2_OPT_TC_UPDATE: h->tc_update = value != 0; return GF2_OK;
     case GF2_OPT_TMA_UPDATE: h->tma = value != 0; return GF2_OK;
+    case GF2_OPT_PLE_BLOCK:
+        if (value < -1 || (value > 0 && value % 64)) return GF2_EINVAL;
+        h->ple_block = value;
+        return GF2_OK;
+    case GF2_OPT_MUL_GEMM_MIN_K:
+        if (value < 0) return GF2_EINVAL;
+        h->gemm_min_k = value;
+        return GF2_OK;
     default: return GF2_EINVAL;
     }
 }

@@ -105,6 +105,7 @@ struct UpdArgs {
     int grid;                  // CTAs to launch (0: one per SM)
     int32_t *err;              // device error word (bounded waits that expire), may be null
     const struct TensorMap2D *tmap;  // TMA descriptor of A's rows (null: plain loads and stores)
+    int64_t W_full;            // PLE: row width; staged rows also get words [W, W_full) (0: none)
 };
 
 // A CUtensorMap (128 bytes) kept opaque outside the files that use TMA.
@@ -141,6 +142,24 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
+// GF(2) product through an FP8 GEMM (kernels_gemm.cu)
+cudaError_t launch_expand_rows(cudaStream_t st, const uint64_t *A, int64_t lda, int64_t rows, int64_t k0, int64_t k,
+                               int64_t kp, uint8_t *out, int num_sms);
+cudaError_t launch_expand_transpose(cudaStream_t st, const uint64_t *B, int64_t ldb, int64_t k0, int64_t k, int64_t n,
+                                    int64_t kp, uint8_t *out, int num_sms);
+cudaError_t launch_parity(cudaStream_t st, const float *D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,
+                          int64_t ldc, int num_sms);
+void *gemm_lt_create();
+void gemm_lt_destroy(void *g);
+int gemm_fp8_counts(void *g, cudaStream_t st, const uint8_t *A8, const uint8_t *B8t, float *D, int64_t rows,
+                    int64_t n, int64_t kp, int64_t ldd);
+// blocked PLE (kernels_blocked.cu)
+cudaError_t launch_gather_lbits(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int64_t row0, int64_t rows,
+                                int64_t c0, int64_t kb, int64_t kw, uint64_t *out, int num_sms);
+cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *descs, int s0,
+                                    int s1, int64_t w_lo, int64_t W);
+cudaError_t launch_trsm_diag(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int nt, const uint64_t *Lt,
+                             int64_t ldt, int64_t t, int64_t w_lo, int64_t W, int num_sms);
 cudaError_t launch_m4ri_prep(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *G,
                              uint64_t *IDX, int64_t m, int num_sms);

@@ -1,0 +1,244 @@
+// kernels_gemm.cu -- the GF(2) product C ^= A B on the tensor cores through a
+// plain library FP8 GEMM, for large inner dimensions.
+//
+// Over GF(2), (A B)[i][j] is the parity of the integer count
+// sum_k A[i][k] B[k][j].  With every bit written as an FP8 E4M3 value 0 or
+// 1.0, an FP8 GEMM with fp32 accumulation returns that count exactly (every
+// partial sum is an integer below 2^24), and its low bit is the GF(2) entry.
+// The library only multiplies; the bit work is here:
+//   * expand_rows_kernel: rows of bits -> rows of FP8 bytes, K-major (the
+//     layout the FP8 GEMM wants for both operands);
+//   * expand_transpose_kernel: B (k x n bits) -> B^T as n rows of k FP8
+//     bytes, transposing 64 x 64 bit blocks with warp shuffles;
+//   * parity_kernel: each fp32 count -> its parity bit, 64 per word, XORed
+//     into C (so C accumulates).
+#include "common.cuh"
+
+#include <cublasLt.h>
+
+#include <new>
+
+namespace gf2 {
+
+namespace {
+
+// 4 bits -> 4 FP8 bytes (1.0 = 0x38 where the bit is set)
+__device__ __forceinline__ uint32_t nib_fp8(uint32_t b)
+{
+    uint32_t t = (b & 15u) * 0x01010101u;   // the nibble in every byte
+    t &= 0x08040201u;                       // byte i keeps bit i
+    t = ((t + 0x7F7F7F7Fu) & 0x80808080u) >> 7;   // 1 in the bytes whose bit was set
+    return t * 0x38u;
+}
+
+// 64 bits -> 64 FP8 bytes at dst (16-byte aligned)
+__device__ __forceinline__ void store_word_fp8(uint8_t *dst, uint64_t w)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t h = (uint32_t)(w >> (16 * q));
+        uint4 v;
+        v.x = nib_fp8(h);
+        v.y = nib_fp8(h >> 4);
+        v.z = nib_fp8(h >> 8);
+        v.w = nib_fp8(h >> 12);
+        *reinterpret_cast<uint4 *>(dst + 16 * q) = v;
+    }
+}
+
+__device__ __forceinline__ unsigned transpose32_g(unsigned x)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const unsigned m = masks[k];
+        const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+}  // namespace
+
+// out[i][0 .. kp) = FP8 of bits k0 .. k0+kp of row i (zero past k)
+__global__ void expand_rows_kernel(const uint64_t *__restrict__ A, int64_t lda, int64_t rows, int64_t k0,
+                                   int64_t k, int64_t kp, uint8_t *__restrict__ out)
+{
+    const int64_t wpr = kp >> 6;                       // words per output row
+    const int64_t total = rows * wpr;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / wpr, w = t - i * wpr;
+        const int64_t kb = k0 + 64 * w;                // first bit of this word (multiple of 64)
+        uint64_t v = 0;
+        if (kb < k) {
+            v = A[i * lda + (kb >> 6)];
+            if (k - kb < 64) v &= (1ull << (k - kb)) - 1ull;
+        }
+        store_word_fp8(out + i * kp + 64 * w, v);
+    }
+}
+
+// out[j][0 .. kp) = FP8 of column j of B over rows k0 .. k0+kp (zero past k).
+// One warp per 64 x 64 bit block: lanes load rows kr and kr+32 of the block,
+// four 32 x 32 shuffle transposes give lane c the columns c and 32 + c.
+__global__ void expand_transpose_kernel(const uint64_t *__restrict__ B, int64_t ldb, int64_t k0, int64_t k,
+                                        int64_t n, int64_t kp, uint8_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nbk = kp >> 6, nbn = (n + 63) >> 6;
+    const int64_t total = nbk * nbn;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t blk = wid; blk < total; blk += nw) {
+        const int64_t bk = blk / nbn, bn = blk - bk * nbn;
+        const int64_t r0 = k0 + 64 * bk + lane, r1 = r0 + 32;
+        const uint64_t x0 = (r0 < k) ? B[r0 * ldb + bn] : 0ull;
+        const uint64_t x1 = (r1 < k) ? B[r1 * ldb + bn] : 0ull;
+        const unsigned t00 = transpose32_g((unsigned)x0), t01 = transpose32_g((unsigned)(x0 >> 32));
+        const unsigned t10 = transpose32_g((unsigned)x1), t11 = transpose32_g((unsigned)(x1 >> 32));
+        // lane c: column 64 bn + c over the block's 64 rows, and column 64 bn + 32 + c
+        const int64_t c0 = 64 * bn + lane, c1 = c0 + 32;
+        if (c0 < n) store_word_fp8(out + c0 * kp + 64 * bk, ((uint64_t)t10 << 32) | t00);
+        if (c1 < n) store_word_fp8(out + c1 * kp + 64 * bk, ((uint64_t)t11 << 32) | t01);
+    }
+}
+
+// C[i][w] ^= parity bits of D[i][64 w .. 64 w + 63] (fp32 integer counts < 2^23).
+// One warp per output word: two coalesced 32-float loads and two ballots.
+__global__ void parity_kernel(const float *__restrict__ D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,
+                              int64_t ldc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t W = (n + 63) >> 6;
+    const int64_t total = rows * W;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = wid; t < total; t += nw) {
+        const int64_t i = t / W, w = t - i * W;
+        const int64_t j0 = 64 * w + lane, j1 = j0 + 32;
+        const float f0 = (j0 < n) ? D[i * ldd + j0] : 0.f;
+        const float f1 = (j1 < n) ? D[i * ldd + j1] : 0.f;
+        // adding 2^23 puts the integer count in the low mantissa bits
+        const unsigned lo = __ballot_sync(0xffffffffu, __float_as_uint(f0 + 8388608.0f) & 1u);
+        const unsigned hi = __ballot_sync(0xffffffffu, __float_as_uint(f1 + 8388608.0f) & 1u);
+        if (lane == 0) C[i * ldc + w] ^= ((uint64_t)hi << 32) | lo;
+    }
+}
+
+cudaError_t launch_expand_rows(cudaStream_t st, const uint64_t *A, int64_t lda, int64_t rows, int64_t k0, int64_t k,
+                               int64_t kp, uint8_t *out, int num_sms)
+{
+    const int64_t total = rows * (kp >> 6);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 16 * num_sms) blocks = 16 * num_sms;
+    if (blocks < 1) blocks = 1;
+    expand_rows_kernel<<<(int)blocks, 256, 0, st>>>(A, lda, rows, k0, k, kp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_transpose(cudaStream_t st, const uint64_t *B, int64_t ldb, int64_t k0, int64_t k, int64_t n,
+                                    int64_t kp, uint8_t *out, int num_sms)
+{
+    const int64_t warps = (kp >> 6) * ((n + 63) >> 6);
+    int64_t blocks = (warps * 32 + 255) / 256;
+    if (blocks > 16 * num_sms) blocks = 16 * num_sms;
+    if (blocks < 1) blocks = 1;
+    expand_transpose_kernel<<<(int)blocks, 256, 0, st>>>(B, ldb, k0, k, n, kp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parity(cudaStream_t st, const float *D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,
+                          int64_t ldc, int num_sms)
+{
+    const int64_t warps = rows * ((n + 63) >> 6);
+    int64_t blocks = (warps * 32 + 255) / 256;
+    if (blocks > 16 * num_sms) blocks = 16 * num_sms;
+    if (blocks < 1) blocks = 1;
+    parity_kernel<<<(int)blocks, 256, 0, st>>>(D, ldd, rows, n, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace gf2
+
+// ---------------------------------------------------------------------------
+// The FP8 GEMM: D (rows x n, row-major, ld ldd, fp32) = A8 (rows x kp bytes,
+// K-major) times B8t^T (B8t: n x kp bytes, K-major), by cuBLASLt.  In
+// cuBLASLt's column-major terms this is D^T (n x rows) = op(B8t) op(A8) with
+// op = transpose for the first operand, both K-major ("TN"); scales are 1.
+
+namespace gf2 {
+
+struct GemmLt {
+    cublasLtHandle_t lt = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+void *gemm_lt_create()
+{
+    GemmLt *g = new (std::nothrow) GemmLt();
+    if (!g) return nullptr;
+    if (cublasLtCreate(&g->lt) != CUBLAS_STATUS_SUCCESS) {
+        delete g;
+        return nullptr;
+    }
+    g->ws_bytes = size_t(64) << 20;
+    if (cudaMalloc(&g->ws, g->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cublasLtDestroy(g->lt);
+        delete g;
+        return nullptr;
+    }
+    return g;
+}
+
+void gemm_lt_destroy(void *p)
+{
+    GemmLt *g = static_cast<GemmLt *>(p);
+    if (!g) return;
+    cudaFree(g->ws);
+    cublasLtDestroy(g->lt);
+    delete g;
+}
+
+// 0 on success, otherwise a cublasStatus_t value (never 0)
+int gemm_fp8_counts(void *p, cudaStream_t st, const uint8_t *A8, const uint8_t *B8t, float *D, int64_t rows,
+                    int64_t n, int64_t kp, int64_t ldd)
+{
+    GemmLt *g = static_cast<GemmLt *>(p);
+    cublasLtMatmulDesc_t op = nullptr;
+    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, ld = nullptr;
+    cublasLtMatmulPreference_t pref = nullptr;
+    cublasStatus_t s = cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F);
+    const cublasOperation_t ta = CUBLAS_OP_T, tb = CUBLAS_OP_N;
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &ta, sizeof(ta));
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &tb, sizeof(tb));
+    // first operand: B8t, kp x n column-major (ld kp), transposed -> n x kp
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasLtMatrixLayoutCreate(&la, CUDA_R_8F_E4M3, kp, n, kp);
+    // second operand: A8, kp x rows column-major (ld kp)
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasLtMatrixLayoutCreate(&lb, CUDA_R_8F_E4M3, kp, rows, kp);
+    // result: n x rows column-major (ld ldd) = rows x n row-major
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasLtMatrixLayoutCreate(&ld, CUDA_R_32F, n, rows, ldd);
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasLtMatmulPreferenceCreate(&pref);
+    if (s == CUBLAS_STATUS_SUCCESS)
+        s = cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &g->ws_bytes,
+                                                 sizeof(g->ws_bytes));
+    cublasLtMatmulHeuristicResult_t res{};
+    int found = 0;
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasLtMatmulAlgoGetHeuristic(g->lt, op, la, lb, ld, ld, pref, 1, &res, &found);
+    if (s == CUBLAS_STATUS_SUCCESS && found == 0) s = CUBLAS_STATUS_NOT_SUPPORTED;
+    const float alpha = 1.0f, beta = 0.0f;
+    if (s == CUBLAS_STATUS_SUCCESS)
+        s = cublasLtMatmul(g->lt, op, &alpha, B8t, la, A8, lb, &beta, D, ld, D, ld, &res.algo, g->ws, g->ws_bytes, st);
+    if (pref) cublasLtMatmulPreferenceDestroy(pref);
+    if (ld) cublasLtMatrixLayoutDestroy(ld);
+    if (lb) cublasLtMatrixLayoutDestroy(lb);
+    if (la) cublasLtMatrixLayoutDestroy(la);
+    if (op) cublasLtMatmulDescDestroy(op);
+    return s == CUBLAS_STATUS_SUCCESS ? 0 : (int)s;
+}
+
+}  // namespace gf2

@@ -89,11 +89,13 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
             for (int64_t w = w_lo + threadIdx.x; w < W; w += blockDim.x) a.A[(r + p) * a.ld + w] = a.B[p * a.ldb + w];
     }
     // PLE: staged rows get their left part (old L bits, new L bits, stripe)
+    // and the words past the updated range
     if (a.mode == UPD_PLE) {
         for (int k = blockIdx.x; k < nS; k += gridDim.x) {
             const uint64_t *src = a.S + (int64_t)k * a.ldS;
             uint64_t *dst = a.A + (r + d->S_off[k]) * a.ld;
             for (int64_t w = threadIdx.x; w < w_lo; w += blockDim.x) dst[w] = src[w];
+            for (int64_t w = W + threadIdx.x; w < a.W_full; w += blockDim.x) dst[w] = src[w];
         }
     }
 
@@ -273,6 +275,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
             const uint64_t *src = a.S + (int64_t)k * a.ldS;
             uint64_t *dst = a.A + (r + d->S_off[k]) * a.ld;
             for (int64_t w = threadIdx.x; w < w_lo; w += blockDim.x) dst[w] = src[w];
+            for (int64_t w = W + threadIdx.x; w < a.W_full; w += blockDim.x) dst[w] = src[w];
         }
     }
 

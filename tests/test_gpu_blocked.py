@@ -1,0 +1,70 @@
+"""The blocked PLE (GF2_OPT_PLE_BLOCK): stripes decomposed block by block,
+each block's trailing update applied at once (TRSM + GF(2) product).  The
+decomposition is unique, so every output must equal the oracle's bit for bit,
+for every block width, including rank-deficient blocks whose pivot rows are
+not word aligned."""
+import numpy as np
+import pytest
+
+import gf2inputs as gi
+import oracle
+from tests.gpu_util import to_dev, to_host, vec_dev
+from tests.test_gpu_parity import assert_ple_equal, make, ref_ple
+
+pytestmark = pytest.mark.gpu
+
+
+def handle(block, gemm_min_k=None):
+    import paper_1111_6549_gb300 as g
+    h = g.Handle()
+    h.set_option(g.OPT_PLE_BLOCK, block)
+    if gemm_min_k is not None:
+        h.set_option(g.OPT_MUL_GEMM_MIN_K, gemm_min_k)
+    return h
+
+
+def run(h, A, m, n, ld_extra=0):
+    W = gi.words_for(n)
+    dA = to_dev(A, W + ld_extra)
+    P, Q = vec_dev(m), vec_dev(min(m, n))
+    r = h.ple(dA, m, n, P, Q)
+    return r, to_host(dA, W), P.cpu().numpy()[:m], Q.cpu().numpy()[:min(m, n)]
+
+
+@pytest.mark.parametrize("block", [64, 128, 256, 1024])
+@pytest.mark.parametrize("kind,m,n", [("dense", 1000, 1500), ("lowrank", 700, 900), ("lastrow_pivot", 600, 800),
+                                      ("sparse", 900, 1300), ("zerocols", 800, 1000), ("dense", 1500, 700),
+                                      ("duprows", 640, 640)])
+def test_blocked_ple_matches_oracle(block, kind, m, n):
+    A = make(kind, m, n, seed=block + m)
+    assert_ple_equal(run(handle(block), A, m, n), ref_ple(A, m, n))
+
+
+@pytest.mark.parametrize("gemm_min_k", [1, 0])
+def test_blocked_ple_gemm_and_table_products(gemm_min_k):
+    """The block's product through the FP8 GEMM (min k 1) and through the tables (0)."""
+    m, n = 3000, 2049
+    A = make("dense", m, n, seed=3)
+    assert_ple_equal(run(handle(512, gemm_min_k), A, m, n, ld_extra=1), ref_ple(A, m, n))
+
+
+def test_blocked_rref_and_solve():
+    h = handle(256, 1)
+    m, n = 2000, 2300
+    A = make("lowrank", m, n, seed=9)
+    dR = to_dev(A)
+    Q = vec_dev(min(m, n))
+    r = h.rref(dR, m, n, Q)
+    R0 = A.copy()
+    r0, Q0 = oracle.rref(R0, m, n)
+    assert r == r0 and np.array_equal(to_host(dR, gi.words_for(n)), R0)
+    nn, nrhs = 1500, 40
+    As = make("dense", nn, nn, seed=4)
+    Bs = gi.bernoulli_matrix(nn, nrhs, 5)
+    dA, dB = to_dev(As), to_dev(Bs)
+    st = h.solve(dA, dB, nn, nrhs)
+    A0, B0 = As.copy(), Bs.copy()
+    st0, _ = oracle.solve(A0, B0, nn, nrhs)
+    assert st == st0
+    if st0 != oracle.SOLVE_INCONSISTENT:
+        assert np.array_equal(to_host(dB, gi.words_for(nrhs)), B0)

@@ -43,7 +43,11 @@ def prefix_check(A, LE, P, Q, r, m, n, c0=1024):
         assert np.array_equal(LE[r0:, wr] & mask, Ap[r0:, wr] & mask)
 
 
-def ple_and_rref_checked(h, A, m, n, expect_rank=None):
+def ple_and_rref_checked(h, A, m, n, expect_rank=None, block=None):
+    if block is not None:
+        import paper_1111_6549_gb300 as g
+        h = g.Handle()
+        h.set_option(g.OPT_PLE_BLOCK, block)
     dA = to_dev(A)
     P, Q = vec_dev(m), vec_dev(min(m, n))
     r = h.ple(dA, m, n, P, Q)
@@ -90,3 +94,11 @@ def test_structured_rank_8192(h):
 def test_sparse_square_32768(h):
     A = gi.sparse_square(32768)
     ple_and_rref_checked(h, A, 32768, 32768)
+
+
+@pytest.mark.parametrize("block", [8192, 16384])
+def test_dense_square_blocked_fullsize(h, block):
+    """The blocked PLE (block trailing updates through the FP8 GEMM) at 65536^2."""
+    A = gi.dense_square(65536)
+    r = ple_and_rref_checked(h, A, 65536, 65536, block=block)
+    assert 65536 - 8 <= r <= 65536

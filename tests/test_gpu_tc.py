@@ -87,3 +87,33 @@ def test_tma_update_ple_rref_and_mul(m, n):
     want = C0.copy()
     oracle.mul(X, B, m, k, n, C=want, accumulate=True)
     assert np.array_equal(to_host(dC), want)
+
+
+@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (128, 64, 256), (300, 70, 300), (129, 65, 257), (1000, 5000, 1000),
+                                   (513, 4099, 300), (2048, 130, 4100), (64, 0, 64)])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_mul_through_fp8_gemm(m, k, n, accumulate):
+    """gf2_mul through the exact FP8 GEMM (forced for every k)."""
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    hh.set_option(g.OPT_MUL_GEMM_MIN_K, 1)
+    A = gi.bernoulli_matrix(m, k, 21) if k else np.zeros((m, 1), np.uint64)
+    B = gi.bernoulli_matrix(k, n, 22) if k else np.zeros((1, gi.words_for(n)), np.uint64)
+    C0 = gi.bernoulli_matrix(m, n, 23)
+    dC = to_dev(C0)
+    hh.mul(dC, to_dev(A), to_dev(B), m, k, n, accumulate=accumulate)
+    want = C0.copy() if accumulate else np.zeros_like(C0)
+    if k:
+        oracle.mul(A, B, m, k, n, C=want, accumulate=accumulate)
+    assert np.array_equal(to_host(dC), want)
+
+
+def test_mul_default_large_k_matches_oracle():
+    """Default options: a large inner dimension takes the FP8 GEMM path."""
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    m, k, n = 700, 9000, 1100
+    A, B = gi.bernoulli_matrix(m, k, 31), gi.bernoulli_matrix(k, n, 32)
+    dC = to_dev(np.zeros((m, gi.words_for(n)), np.uint64))
+    hh.mul(dC, to_dev(A), to_dev(B), m, k, n)
+    assert np.array_equal(to_host(dC), oracle.mul(A, B, m, k, n))
