@@ -545,6 +545,7 @@ def run_ours(args):
                 "update_share_of_step_diagnostic": None,
                 "kernel_ms_per_step_diagnostic": {k: sd[k + "_ms"] / diag_steps
                                                   for k in ("update", "panel", "prep", "rref_prep", "other")},
+                "algorithmic_bytes_per_step_diagnostic": sd["update_bytes"] / diag_steps,
                 "note": "achieved = algorithmic bytes / CUDA-event time of every 7th update launch "
                         "of the timed steps (events on the launching stream); the per-kind breakdown "
                         "comes from a separate pass with every launch bracketed by events (panels "

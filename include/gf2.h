@@ -349,6 +349,16 @@ int gf2_set_profiling(gf2_handle_t handle, int on);
 int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);
 int gf2_reset_stats(gf2_handle_t handle);
 
+/*
+ * Failure-detection self-test (no counterpart in the paper): runs one kernel
+ * whose bounded mbarrier wait -- the wait the tcgen05 and TMA kernels use --
+ * can only end by its limit (limit_us microseconds, at most 10^6), exactly as
+ * when an asynchronous copy or product never completes.  Returns
+ * GF2_ETIMEOUT when the wait expired and was reported (the expected result);
+ * the handle stays usable.  GF2_EINVAL for a bad limit.
+ */
+int gf2_selftest_wait(gf2_handle_t handle, int64_t limit_us);
+
 /* Static name of a status code. */
 const char *gf2_strerror(int code);
 

@@ -105,6 +105,7 @@ def load():
             "gf2_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "gf2_solve_async": ([vp, vp, i64, i64, vp, i64, i64, vp], ctypes.c_int),
             "gf2_set_option": ([vp, ctypes.c_int, i64], ctypes.c_int),
+            "gf2_selftest_wait": ([vp, i64], ctypes.c_int),
             "gf2_batched_config": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "gf2_batched_get_config": ([vp, i32p], ctypes.c_int),
             "gf2_batched_autotune": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -323,6 +324,11 @@ class Handle:
         self._bind_stream()
         _check(load().gf2_rref_host(self._h, aptr, m, n, ld, qptr, ctypes.byref(rank)), "gf2_rref_host")
         return rank.value
+
+    def selftest_wait(self, limit_us: int = 1000) -> int:
+        """Run the bounded-wait self-test; returns the status code (GF2_ETIMEOUT expected)."""
+        self._bind_stream()
+        return int(load().gf2_selftest_wait(self._h, int(limit_us)))
 
     def set_option(self, option: int, value: int) -> None:
         """OPT_LOOKAHEAD / OPT_TC_MUL / OPT_TC_UPDATE / OPT_TMA_UPDATE (0 off, 1 on); results are identical."""

@@ -1335,6 +1335,15 @@ int gf2_rref_host(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld,
     return finish_sync(h);
 }
 
+int gf2_selftest_wait(gf2_handle_t h, int64_t limit_us)
+{
+    if (!h || limit_us < 0 || limit_us > 1000000) return GF2_EINVAL;
+    DeviceGuard g(h->device);
+    CK(launch_wait_selftest(h->stream, err_dev(h), (unsigned long long)limit_us * 1000ull));
+    h->launches += 1;
+    return finish_sync(h);
+}
+
 int gf2_set_option(gf2_handle_t h, int option, int64_t value)
 {
     if (!h) return GF2_EINVAL;

@@ -38,13 +38,14 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t phase)
     return ok != 0;
 }
 
-// Wait for the given phase parity; false after ASYNC_WAIT_NS without it.
-__device__ __forceinline__ bool mbar_wait_limited(uint64_t *bar, uint32_t phase)
+// Wait for the given phase parity; false after limit_ns without it.
+__device__ __forceinline__ bool mbar_wait_limited(uint64_t *bar, uint32_t phase,
+                                                  unsigned long long limit_ns = ASYNC_WAIT_NS)
 {
     if (mbar_test(bar, phase)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_test(bar, phase))
-        if (global_ns() - t0 > ASYNC_WAIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 

@@ -160,6 +160,7 @@ cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, co
                                     int s1, int64_t w_lo, int64_t W);
 cudaError_t launch_trsm_diag(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int nt, const uint64_t *Lt,
                              int64_t ldt, int64_t t, int64_t w_lo, int64_t W, int num_sms);
+cudaError_t launch_wait_selftest(cudaStream_t st, int32_t *err, unsigned long long limit_ns);
 cudaError_t launch_m4ri_prep(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *G,
                              uint64_t *IDX, int64_t m, int num_sms);

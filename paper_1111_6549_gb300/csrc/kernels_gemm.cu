@@ -107,24 +107,34 @@ __global__ void expand_transpose_kernel(const uint64_t *__restrict__ B, int64_t 
 }
 
 // C[i][w] ^= parity bits of D[i][64 w .. 64 w + 63] (fp32 integer counts < 2^23).
-// One warp per output word: two coalesced 32-float loads and two ballots.
+// One warp per group of PAR_WORDS output words of a row: all of their
+// coalesced 32-float loads are issued before the ballots.
+constexpr int PAR_WORDS = 4;
+
 __global__ void parity_kernel(const float *__restrict__ D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,
                               int64_t ldc)
 {
     const int lane = threadIdx.x & 31;
     const int64_t W = (n + 63) >> 6;
-    const int64_t total = rows * W;
+    const int64_t G = (W + PAR_WORDS - 1) / PAR_WORDS;
+    const int64_t total = rows * G;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = wid; t < total; t += nw) {
-        const int64_t i = t / W, w = t - i * W;
-        const int64_t j0 = 64 * w + lane, j1 = j0 + 32;
-        const float f0 = (j0 < n) ? D[i * ldd + j0] : 0.f;
-        const float f1 = (j1 < n) ? D[i * ldd + j1] : 0.f;
-        // adding 2^23 puts the integer count in the low mantissa bits
-        const unsigned lo = __ballot_sync(0xffffffffu, __float_as_uint(f0 + 8388608.0f) & 1u);
-        const unsigned hi = __ballot_sync(0xffffffffu, __float_as_uint(f1 + 8388608.0f) & 1u);
-        if (lane == 0) C[i * ldc + w] ^= ((uint64_t)hi << 32) | lo;
+        const int64_t i = t / G, w0 = (t - i * G) * PAR_WORDS;
+        float f[2 * PAR_WORDS];
+#pragma unroll
+        for (int q = 0; q < 2 * PAR_WORDS; ++q) {
+            const int64_t j = 64 * w0 + 32 * q + lane;
+            f[q] = (j < n) ? D[i * ldd + j] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < PAR_WORDS; ++q) {
+            // adding 2^23 puts the integer count in the low mantissa bits
+            const unsigned lo = __ballot_sync(0xffffffffu, __float_as_uint(f[2 * q] + 8388608.0f) & 1u);
+            const unsigned hi = __ballot_sync(0xffffffffu, __float_as_uint(f[2 * q + 1] + 8388608.0f) & 1u);
+            if (lane == q && w0 + q < W) C[i * ldc + w0 + q] ^= ((uint64_t)hi << 32) | lo;
+        }
     }
 }
 
@@ -153,7 +163,7 @@ cudaError_t launch_expand_transpose(cudaStream_t st, const uint64_t *B, int64_t 
 cudaError_t launch_parity(cudaStream_t st, const float *D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,
                           int64_t ldc, int num_sms)
 {
-    const int64_t warps = rows * ((n + 63) >> 6);
+    const int64_t warps = rows * ((((n + 63) >> 6) + PAR_WORDS - 1) / PAR_WORDS);
     int64_t blocks = (warps * 32 + 255) / 256;
     if (blocks > 16 * num_sms) blocks = 16 * num_sms;
     if (blocks < 1) blocks = 1;
