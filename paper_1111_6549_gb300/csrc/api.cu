@@ -836,31 +836,15 @@ int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t
         CK(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)Wc * 8, (size_t)m, h->stream));
     if (!h->tc_mul && h->gemm_min_k > 0 && k >= h->gemm_min_k) return mul_gemm(h, C, ldc, A, lda, B, ldb, m, k, n);
     if (h->tc_mul && k > 0) {
-        // tensor cores: every 64-column chunk of A accumulates into the same
-        // counts in tensor memory, so C is read and written once per group of
-        // up to 2^22 columns of A (fp32 counts stay exact below 2^24)
+        // tensor cores, pipelined tcgen05 kernel: the counts of every inner
+        // chunk accumulate in tensor memory, so C is read and written once per
+        // group of up to 2^22 columns of A (fp32 counts stay exact below 2^24)
         constexpr int64_t KG = int64_t(1) << 22;
         for (int64_t k0 = 0; k0 < k; k0 += KG) {
-            UpdArgs a{};
-            a.tp_lo = 0;
-            a.tp_hi = -1;
-            a.left_copies = 1;
-            a.mode = UPD_MUL;
-            a.A = C;
-            a.ld = ldc;
-            a.m = m;
-            a.W = Wc;
-            a.idx = A + k0 / 64;
-            a.idx_stride = lda;
-            a.B = B + k0 * ldb;
-            a.ldb = ldb;
-            a.gen_count = std::min(KG, k - k0);
-            a.row_lo = 0;
-            a.row_hi = m;
-            a.w_lo = 0;
-            a.bytes = bytes_dev(h);
-            const int rc = launch_update_counted(h, a);
-            if (rc) return rc;
+            Timed t(h, K_OTHER);
+            CK(launch_tc_mul(h->stream, C, ldc, A + k0 / 64, lda, B + k0 * ldb, ldb, m, std::min(KG, k - k0), n,
+                             err_dev(h), h->num_sms));
+            h->launches += 1;
         }
         return GF2_OK;
     }

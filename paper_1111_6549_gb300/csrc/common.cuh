@@ -135,6 +135,8 @@ cudaError_t setup_prep_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
 bool update_vectorised(const UpdArgs &a);   // true when the paired, pipelined form runs
 cudaError_t launch_update_tc(cudaStream_t st, const UpdArgs &a, int num_sms);
+cudaError_t launch_tc_mul(cudaStream_t st, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
+                          int64_t ldb, int64_t m, int64_t k, int64_t n, int32_t *err, int num_sms);
 cudaError_t setup_update_tma_kernel();
 cudaError_t launch_update_tma(cudaStream_t st, const UpdArgs &a, int grid);   // a.tmap must be set
 cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t W, int64_t ld,

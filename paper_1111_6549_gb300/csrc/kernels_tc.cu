@@ -22,6 +22,8 @@
 // the error word, frees its tensor memory and returns.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace gf2 {
 
 namespace {
@@ -324,6 +326,234 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_update_kernel(UpdArgs a)
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------
+// The product C ^= A B (A: m x k bits, B: k x n bits) as a pipelined tcgen05
+// kernel.  Per CTA output tile of 256 rows x 256 columns, two M = 128
+// accumulators (all 512 tensor-memory columns) share each expanded chunk of
+// B; per chunk of 64 inner-dimension bits all 512 threads expand their
+// operand bits to FP8 (arithmetic nibble spread, no table lookups) into one
+// of two shared-memory stages while the MMAs of the previous chunk run from
+// the other stage; one thread issues the eight MMAs of a chunk and commits
+// them to that stage's mbarrier, which frees the stage again.  The operand
+// bits come through a shared-memory ring filled by cp.async seven chunks
+// ahead (a load that ends in a register would stall the chunk on memory
+// latency).  The epilogue takes
+// each count's parity (count + 2^23) and XORs 64 of them per word into C.
+constexpr int TM_THREADS = 512;
+constexpr int TM_A_BYTES = TC_M * TC_KC;                     // 8 KiB: 128 rows x 64 bytes
+constexpr int TM_STAGE_BYTES = 2 * TM_A_BYTES + TC_B_BYTES;  // 32 KiB
+constexpr uint32_t TM_TMEM_COLS = 512;
+constexpr int TM_RING = 8;                                   // chunks of operand bits in flight
+constexpr int TM_RING_WORDS = 256 + 64 * 4;                  // A: 256 rows, B: 64 rows x 4 words
+constexpr size_t TM_SMEM_BYTES = 116 * 1024;                 // 2 stages + the bit ring (+ room: one CTA per SM)
+static_assert(2 * TM_STAGE_BYTES + TM_RING * TM_RING_WORDS * 8 + 1024 <= TM_SMEM_BYTES, "tc_mul shared memory");
+
+struct TcMulArgs {
+    uint64_t *C;
+    int64_t ldc;
+    const uint64_t *A;
+    int64_t lda;
+    const uint64_t *B;
+    int64_t ldb;
+    int64_t m, k, n;
+    int32_t *err;
+};
+
+namespace {
+
+// 4 bits -> 4 FP8 bytes (1.0 = 0x38 where the bit is set)
+__device__ __forceinline__ uint32_t nib_fp8_tc(uint32_t b)
+{
+    uint32_t t = (b & 15u) * 0x01010101u;
+    t &= 0x08040201u;
+    t = ((t + 0x7F7F7F7Fu) & 0x80808080u) >> 7;
+    return t * 0x38u;
+}
+
+// 32 bits -> K groups j0 and j0 + 1 (16 bytes each) of a row in the core-matrix layout
+__device__ __forceinline__ void expand_store_half(uint8_t *tile, int row, int j0, uint32_t bits)
+{
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const uint32_t h = bits >> (16 * q);
+        uint4 v;
+        v.x = nib_fp8_tc(h);
+        v.y = nib_fp8_tc(h >> 4);
+        v.z = nib_fp8_tc(h >> 8);
+        v.w = nib_fp8_tc(h >> 12);
+        *reinterpret_cast<uint4 *>(tile + core_off(row, j0 + q)) = v;
+    }
+}
+
+__device__ __forceinline__ void cp_async8_tc(void *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr(dst)), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_tc() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_tc() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+}  // namespace
+
+__global__ void __launch_bounds__(TM_THREADS, 1) tc_mul_kernel(TcMulArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t tm_smem[];
+    __shared__ __align__(8) uint64_t sfree[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint8_t *stage0 = tm_smem + ((1024u - (saddr(tm_smem) & 1023u)) & 1023u);
+    uint64_t *ring = reinterpret_cast<uint64_t *>(stage0 + 2 * TM_STAGE_BYTES);
+
+    if (tid == 0) {
+        mbar_init(&sfree[0], 1);
+        mbar_init(&sfree[1], 1);
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(&tmem_base)),
+                     "r"(TM_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    const int64_t m = a.m, k = a.k, n = a.n;
+    const int64_t Wc = (n + 63) >> 6;
+    const int64_t KC = (k + 63) >> 6;
+    const int64_t NTX = (n + 255) >> 8, NTY = (m + 255) >> 8;
+    const int64_t T = NTX * NTY;
+    // work split per chunk: thread t expands 32 bits of A row t / 2 (K groups
+    // 2 (t & 1) and up); warp w transposes a 32 x 32 block of B -- generator
+    // rows 32 (w & 1) .., columns 64 (w / 4) + 32 ((w / 2) & 1) .. -- and each
+    // lane expands the 32 bits of one column into K groups 2 (w & 1) and up
+    const int arow = tid >> 1, ahalf = tid & 1;
+    const int bword = warp >> 2, bchalf = (warp >> 1) & 1, bkhalf = warp & 1;
+    int64_t g = 0;                                   // chunks issued by this CTA so far
+    for (int64_t t = blockIdx.x; t < T && KC > 0; t += gridDim.x) {
+        const int64_t tx = t / NTY, ty = t - tx * NTY;   // neighbouring CTAs share a column tile of B
+        const int64_t row0 = ty * 256, wb = tx * 4;
+        // operand bits, chunk kc in ring slot kc % TM_RING: A rows (256
+        // words) then B's 64 generator rows x 4 words, copied by cp.async
+        // TM_RING - 1 chunks ahead of their expansion
+        const int64_t ia = row0 + (tid >> 1);
+        auto issue = [&](int64_t kc) {
+            uint64_t *slot = ring + (kc % TM_RING) * TM_RING_WORDS;
+            if (kc < KC) {
+                if (tid < 256) {                             // A: row row0 + tid, word kc
+                    const int64_t r = row0 + tid;
+                    const bool ok = r < m;
+                    cp_async8_tc(slot + tid, a.A + (ok ? r : 0) * a.lda + kc, ok);
+                } else {                                     // B: generator row 64 kc + (t >> 2), word wb + (t & 3)
+                    const int u = tid - 256;
+                    const int64_t r = 64 * kc + (u >> 2), w = wb + (u & 3);
+                    const bool ok = r < k && w < Wc;
+                    cp_async8_tc(slot + 256 + u, a.B + (ok ? r * a.ldb + w : 0), ok);
+                }
+            }
+            cp_async_commit_tc();
+        };
+        for (int q = 0; q < TM_RING - 1; ++q) issue(q);
+        cp_async_wait_tc<TM_RING - 2>();                     // chunk 0 has landed (this thread's part)
+        __syncthreads();
+        for (int64_t kc = 0; kc < KC; ++kc) {
+            const int st = (int)(g & 1);
+            const uint64_t *slot = ring + (kc % TM_RING) * TM_RING_WORDS;
+            uint64_t va = slot[tid >> 1];
+            const int64_t rem = k - 64 * kc;
+            if (rem < 64) va &= (1ull << rem) - 1ull;
+            const uint32_t xa = ia < m ? (uint32_t)(va >> (32 * ahalf)) : 0u;
+            const uint32_t xb = (uint32_t)(slot[256 + (32 * bkhalf + lane) * 4 + bword] >> (32 * bchalf));
+            // the MMAs of chunk g - 2 read this stage: wait until they are done
+            if (g >= 2 && !mbar_wait_bounded(&sfree[st], (uint32_t)(((g >> 1) - 1) & 1))) {
+                s_abort = 1;
+                if (a.err) atomicExch(a.err, 4);         // GF2_ETIMEOUT
+            }
+            uint8_t *sA = stage0 + st * TM_STAGE_BYTES;
+            uint8_t *sB = sA + 2 * TM_A_BYTES;
+            expand_store_half(sA + (arow >> 7) * TM_A_BYTES, arow & 127, 2 * ahalf, xa);
+            const unsigned col = transpose32_tc(xb);     // lane c: one column over 32 generator rows
+            expand_store_half(sB, bword * 64 + bchalf * 32 + lane, 2 * bkhalf, col);
+            issue(kc + TM_RING - 1);                     // into the slot chunk kc - 1 used
+            cp_async_wait_tc<TM_RING - 2>();             // chunk kc + 1 has landed
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (s_abort) break;
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = saddr(sA), a1 = a0 + TM_A_BYTES, b0 = saddr(sB);
+#pragma unroll
+                for (int ks = 0; ks < TC_KC / 32; ++ks) {
+                    const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                    mma_f8(tmem, smem_desc(a0 + ks * 256, 128, 512), smem_desc(b0 + ks * 256, 128, 512), acc);
+                    mma_f8(tmem + 256, smem_desc(a1 + ks * 256, 128, 512), smem_desc(b0 + ks * 256, 128, 512), acc);
+                }
+                mma_commit(&sfree[st]);
+            }
+            ++g;
+        }
+        cp_async_wait_tc<0>();
+        if (s_abort) break;
+        // every MMA of the tile has completed once the last chunk's commit has
+        if (!mbar_wait_bounded(&sfree[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1))) {
+            s_abort = 1;
+            if (a.err) atomicExch(a.err, 4);
+        }
+        __syncthreads();
+        if (s_abort) break;
+        tc_fence_after();
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. of
+        // accumulator (w / 4) % 2, columns 128 (w / 8) .. + 127
+        const int quad = warp & 3, accn = (warp >> 2) & 1, chalf = warp >> 3;
+        const int64_t i = row0 + 128 * accn + 32 * quad + lane;
+#pragma unroll 1
+        for (int cb = 0; cb < 4; cb += 2) {
+            uint32_t v0[32], v1[32];
+            const uint32_t base = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(256 * accn + 128 * chalf);
+            tmem_ld32(base + (uint32_t)(cb * 32), v0);
+            tmem_ld32(base + (uint32_t)((cb + 1) * 32), v1);
+            uint32_t p0 = 0, p1 = 0;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                p0 |= (__float_as_uint(__uint_as_float(v0[q]) + 8388608.0f) & 1u) << q;
+                p1 |= (__float_as_uint(__uint_as_float(v1[q]) + 8388608.0f) & 1u) << q;
+            }
+            const int64_t w = wb + 2 * chalf + cb / 2;
+            if (i < m && w < Wc) a.C[i * a.ldc + w] ^= ((uint64_t)p1 << 32) | p0;
+        }
+        tc_fence_before();
+        __syncthreads();                             // tensor memory read out before the next tile's MMAs
+        tc_fence_after();
+    }
+    if (s_abort && g > 0) mbar_wait_bounded(&sfree[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1));
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TM_TMEM_COLS));
+}
+
+cudaError_t launch_tc_mul(cudaStream_t st, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
+                          int64_t ldb, int64_t m, int64_t k, int64_t n, int32_t *err, int num_sms)
+{
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(tc_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TM_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    TcMulArgs a{C, ldc, A, lda, B, ldb, m, k, n, err};
+    const int64_t tiles = ((n + 255) >> 8) * ((m + 255) >> 8);
+    const int grid = (int)std::min<int64_t>(num_sms, std::max<int64_t>(tiles, 1));
+    tc_mul_kernel<<<grid, TM_THREADS, TM_SMEM_BYTES, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_update_tc(cudaStream_t st, const UpdArgs &a, int num_sms)
