@@ -332,23 +332,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_update_kernel(UpdArgs a)
 // The product C ^= A B (A: m x k bits, B: k x n bits) as a pipelined tcgen05
 // kernel.  Per CTA output tile of 256 rows x 256 columns, two M = 128
 // accumulators (all 512 tensor-memory columns) share each expanded chunk of
-// B; per chunk of 64 inner-dimension bits all 512 threads expand their
+// B; per chunk of 128 inner-dimension bits all 512 threads expand their
 // operand bits to FP8 (arithmetic nibble spread, no table lookups) into one
 // of two shared-memory stages while the MMAs of the previous chunk run from
 // the other stage; one thread issues the eight MMAs of a chunk and commits
 // them to that stage's mbarrier, which frees the stage again.  The operand
-// bits come through a shared-memory ring filled by cp.async seven chunks
+// bits come through a shared-memory ring filled by cp.async five chunks
 // ahead (a load that ends in a register would stall the chunk on memory
 // latency).  The epilogue takes
 // each count's parity (count + 2^23) and XORs 64 of them per word into C.
 constexpr int TM_THREADS = 512;
-constexpr int TM_A_BYTES = TC_M * TC_KC;                     // 8 KiB: 128 rows x 64 bytes
-constexpr int TM_STAGE_BYTES = 2 * TM_A_BYTES + TC_B_BYTES;  // 32 KiB
+constexpr int TM_KW = 2;                                     // inner-dimension words per chunk (128 bits)
+constexpr int TM_KB = 64 * TM_KW;                            // FP8 bytes per operand row and chunk
+constexpr int TM_A_BYTES = TC_M * TM_KB;                     // 16 KiB: 128 rows x 128 bytes
+constexpr int TM_B_BYTES = TC_N * TM_KB;                     // 32 KiB: 256 columns x 128 bytes
+constexpr int TM_STAGE_BYTES = 2 * TM_A_BYTES + TM_B_BYTES;  // 64 KiB
 constexpr uint32_t TM_TMEM_COLS = 512;
-constexpr int TM_RING = 8;                                   // chunks of operand bits in flight
-constexpr int TM_RING_WORDS = 256 + 64 * 4;                  // A: 256 rows, B: 64 rows x 4 words
-constexpr size_t TM_SMEM_BYTES = 116 * 1024;                 // 2 stages + the bit ring (+ room: one CTA per SM)
-static_assert(2 * TM_STAGE_BYTES + TM_RING * TM_RING_WORDS * 8 + 1024 <= TM_SMEM_BYTES, "tc_mul shared memory");
+constexpr int TM_RING = 6;                                   // chunks of operand bits in flight
+constexpr int TM_RING_WORDS = 256 * TM_KW + 64 * TM_KW * 4;  // A: 256 rows x 2 words, B: 128 rows x 4 words
+constexpr size_t TM_SMEM_BYTES = 2 * TM_STAGE_BYTES + TM_RING * TM_RING_WORDS * 8 + 1024;
+static_assert(TM_SMEM_BYTES <= 227 * 1024, "tc_mul shared memory");
 
 struct TcMulArgs {
     uint64_t *C;
@@ -372,7 +375,14 @@ __device__ __forceinline__ uint32_t nib_fp8_tc(uint32_t b)
     return t * 0x38u;
 }
 
-// 32 bits -> K groups j0 and j0 + 1 (16 bytes each) of a row in the core-matrix layout
+// Byte offset of (row, 16-byte K group j) in the core-matrix layout of a
+// 128-byte-per-row chunk: K-direction stride 128 bytes, 8-row groups 1024 apart.
+__device__ __forceinline__ uint32_t core_off8(int row, int j)
+{
+    return (uint32_t)(((row >> 3) * 8 + j) * 128 + (row & 7) * 16);
+}
+
+// 32 bits -> K groups j0 and j0 + 1 (16 bytes each) of a row in that layout
 __device__ __forceinline__ void expand_store_half(uint8_t *tile, int row, int j0, uint32_t bits)
 {
 #pragma unroll
@@ -383,7 +393,7 @@ __device__ __forceinline__ void expand_store_half(uint8_t *tile, int row, int j0
         v.y = nib_fp8_tc(h >> 4);
         v.z = nib_fp8_tc(h >> 8);
         v.w = nib_fp8_tc(h >> 12);
-        *reinterpret_cast<uint4 *>(tile + core_off(row, j0 + q)) = v;
+        *reinterpret_cast<uint4 *>(tile + core_off8(row, j0 + q)) = v;
     }
 }
 
@@ -426,35 +436,36 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tc_mul_kernel(TcMulArgs a)
 
     const int64_t m = a.m, k = a.k, n = a.n;
     const int64_t Wc = (n + 63) >> 6;
-    const int64_t KC = (k + 63) >> 6;
+    const int64_t KC = (k + TM_KB - 1) / TM_KB;
     const int64_t NTX = (n + 255) >> 8, NTY = (m + 255) >> 8;
     const int64_t T = NTX * NTY;
-    // work split per chunk: thread t expands 32 bits of A row t / 2 (K groups
-    // 2 (t & 1) and up); warp w transposes a 32 x 32 block of B -- generator
-    // rows 32 (w & 1) .., columns 64 (w / 4) + 32 ((w / 2) & 1) .. -- and each
-    // lane expands the 32 bits of one column into K groups 2 (w & 1) and up
-    const int arow = tid >> 1, ahalf = tid & 1;
-    const int bword = warp >> 2, bchalf = (warp >> 1) & 1, bkhalf = warp & 1;
+    // work split per chunk: thread t expands word t & 1 of A row t / 2 (K
+    // groups 4 (t & 1) .. + 3); warp w transposes two 32 x 32 blocks of B --
+    // generator rows 64 (w & 1) + 32 h (h = 0, 1), columns 64 (w / 4) +
+    // 32 ((w / 2) & 1) .. -- and each lane expands one column's 32 bits per
+    // block into K groups 4 (w & 1) + 2 h and up
+    const int arow = tid >> 1, aword = tid & 1;
+    const int bword = warp >> 2, bchalf = (warp >> 1) & 1, bkq = warp & 1;
     int64_t g = 0;                                   // chunks issued by this CTA so far
     for (int64_t t = blockIdx.x; t < T && KC > 0; t += gridDim.x) {
         const int64_t tx = t / NTY, ty = t - tx * NTY;   // neighbouring CTAs share a column tile of B
         const int64_t row0 = ty * 256, wb = tx * 4;
-        // operand bits, chunk kc in ring slot kc % TM_RING: A rows (256
-        // words) then B's 64 generator rows x 4 words, copied by cp.async
-        // TM_RING - 1 chunks ahead of their expansion
-        const int64_t ia = row0 + (tid >> 1);
+        // operand bits, chunk kc in ring slot kc % TM_RING: A rows (256 x
+        // TM_KW words) then B's 128 generator rows x 4 words, copied by
+        // cp.async TM_RING - 1 chunks ahead of their expansion
+        const int64_t ia = row0 + arow;
         auto issue = [&](int64_t kc) {
             uint64_t *slot = ring + (kc % TM_RING) * TM_RING_WORDS;
             if (kc < KC) {
-                if (tid < 256) {                             // A: row row0 + tid, word kc
-                    const int64_t r = row0 + tid;
-                    const bool ok = r < m;
-                    cp_async8_tc(slot + tid, a.A + (ok ? r : 0) * a.lda + kc, ok);
-                } else {                                     // B: generator row 64 kc + (t >> 2), word wb + (t & 3)
-                    const int u = tid - 256;
-                    const int64_t r = 64 * kc + (u >> 2), w = wb + (u & 3);
+                {                                            // A: row row0 + t / 2, word TM_KW kc + (t & 1)
+                    const int64_t r = row0 + (tid >> 1), w = TM_KW * kc + (tid & 1);
+                    const bool ok = r < m && 64 * w < k;
+                    cp_async8_tc(slot + tid, a.A + (ok ? r * a.lda + w : 0), ok);
+                }
+                {                                            // B: generator row 128 kc + t / 4, word wb + (t & 3)
+                    const int64_t r = (int64_t)TM_KB * kc + (tid >> 2), w = wb + (tid & 3);
                     const bool ok = r < k && w < Wc;
-                    cp_async8_tc(slot + 256 + u, a.B + (ok ? r * a.ldb + w : 0), ok);
+                    cp_async8_tc(slot + 256 * TM_KW + tid, a.B + (ok ? r * a.ldb + w : 0), ok);
                 }
             }
             cp_async_commit_tc();
@@ -465,11 +476,10 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tc_mul_kernel(TcMulArgs a)
         for (int64_t kc = 0; kc < KC; ++kc) {
             const int st = (int)(g & 1);
             const uint64_t *slot = ring + (kc % TM_RING) * TM_RING_WORDS;
-            uint64_t va = slot[tid >> 1];
-            const int64_t rem = k - 64 * kc;
-            if (rem < 64) va &= (1ull << rem) - 1ull;
-            const uint32_t xa = ia < m ? (uint32_t)(va >> (32 * ahalf)) : 0u;
-            const uint32_t xb = (uint32_t)(slot[256 + (32 * bkhalf + lane) * 4 + bword] >> (32 * bchalf));
+            uint64_t va = slot[tid];                         // word aword of A row arow
+            const int64_t rem = k - 64 * (TM_KW * kc + aword);
+            if (rem < 64) va = rem <= 0 ? 0ull : (va & ((1ull << rem) - 1ull));
+            if (ia >= m) va = 0;
             // the MMAs of chunk g - 2 read this stage: wait until they are done
             if (g >= 2 && !mbar_wait_bounded(&sfree[st], (uint32_t)(((g >> 1) - 1) & 1))) {
                 s_abort = 1;
@@ -477,9 +487,16 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tc_mul_kernel(TcMulArgs a)
             }
             uint8_t *sA = stage0 + st * TM_STAGE_BYTES;
             uint8_t *sB = sA + 2 * TM_A_BYTES;
-            expand_store_half(sA + (arow >> 7) * TM_A_BYTES, arow & 127, 2 * ahalf, xa);
-            const unsigned col = transpose32_tc(xb);     // lane c: one column over 32 generator rows
-            expand_store_half(sB, bword * 64 + bchalf * 32 + lane, 2 * bkhalf, col);
+            uint8_t *tA = sA + (arow >> 7) * TM_A_BYTES;
+            expand_store_half(tA, arow & 127, 4 * aword, (uint32_t)va);
+            expand_store_half(tA, arow & 127, 4 * aword + 2, (uint32_t)(va >> 32));
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int kr = 64 * bkq + 32 * hh + lane;    // generator row within the chunk
+                const uint32_t xb = (uint32_t)(slot[256 * TM_KW + kr * 4 + bword] >> (32 * bchalf));
+                const unsigned col = transpose32_tc(xb); // lane c: one column over 32 generator rows
+                expand_store_half(sB, bword * 64 + bchalf * 32 + lane, 4 * bkq + 2 * hh, col);
+            }
             issue(kc + TM_RING - 1);                     // into the slot chunk kc - 1 used
             cp_async_wait_tc<TM_RING - 2>();             // chunk kc + 1 has landed
             fence_async_smem();
@@ -490,10 +507,11 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tc_mul_kernel(TcMulArgs a)
                 tc_fence_after();
                 const uint32_t a0 = saddr(sA), a1 = a0 + TM_A_BYTES, b0 = saddr(sB);
 #pragma unroll
-                for (int ks = 0; ks < TC_KC / 32; ++ks) {
+                for (int ks = 0; ks < TM_KB / 32; ++ks) {
                     const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-                    mma_f8(tmem, smem_desc(a0 + ks * 256, 128, 512), smem_desc(b0 + ks * 256, 128, 512), acc);
-                    mma_f8(tmem + 256, smem_desc(a1 + ks * 256, 128, 512), smem_desc(b0 + ks * 256, 128, 512), acc);
+                    mma_f8(tmem, smem_desc(a0 + ks * 256, 128, 1024), smem_desc(b0 + ks * 256, 128, 1024), acc);
+                    mma_f8(tmem + 256, smem_desc(a1 + ks * 256, 128, 1024), smem_desc(b0 + ks * 256, 128, 1024),
+                           acc);
                 }
                 mma_commit(&sfree[st]);
             }
