@@ -79,7 +79,8 @@ int gf2_set_stream(gf2_handle_t handle, void *stream);
  */
 int gf2_ple(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
             int64_t *P, int64_t *Q, int64_t *rank);
-/* As gf2_ple, but the rank goes to DEVICE memory rank_dev and nothing waits. */
+/* As gf2_ple, but the rank goes to DEVICE memory rank_dev and nothing waits
+   (except, with a PLE block width in effect, once per block for the rank). */
 int gf2_ple_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_t ld_words,
                   int64_t *P, int64_t *Q, int64_t *rank_dev);
 
@@ -114,11 +115,16 @@ int gf2_rref_m4ri_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, 
                         int64_t *Q, int64_t *rank_dev);
 
 /*
- * Product over GF(2) by tabulated row combinations (Section 3.2: the trailing
- * update is the M4RM multiplication of Albrecht, Bard & Hart; Algorithms 5-6).
+ * Product over GF(2) (Section 3.2: the trailing update is the M4RM
+ * multiplication of Albrecht, Bard & Hart; Algorithms 5-6).
  *   C = A B (accumulate = 0) or C ^= A B (accumulate != 0).
  *   A device m x k (lda words), B device k x n (ldb), C device m x n (ldc).
  *   C must not overlap A or B.  Asynchronous.
+ * Inner dimensions below GF2_OPT_MUL_GEMM_MIN_K (default 4096) use the
+ * tabulated row combinations, 64 columns of A per pass over C; larger ones
+ * the exact FP8 GEMM (see the options); GF2_OPT_TC_MUL selects the library's
+ * own tcgen05 kernel instead.  The FP8 GEMM path holds up to about 1 GiB of
+ * fp32 counts plus the expanded operands in the handle's workspace.
  */
 int gf2_mul(gf2_handle_t handle, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda,
             const uint64_t *B, int64_t ldb, int64_t m, int64_t k, int64_t n, int accumulate);
@@ -289,8 +295,9 @@ int gf2_server_destroy(gf2_server_t server);
  * Execution options of a handle (value 0 = off, 1 = on):
  *   GF2_OPT_LOOKAHEAD  overlap each stripe's pivot search with the previous
  *                      stripe's trailing update on a side stream (default on)
- *   GF2_OPT_TC_MUL     gf2_mul on the tensor cores: 0/1 operands in FP8, the
- *                      counts accumulated in tensor memory and reduced mod 2
+ *   GF2_OPT_TC_MUL     gf2_mul on the library's own tcgen05 kernel: 0/1
+ *                      operands expanded to FP8 in shared memory, the counts
+ *                      accumulated in tensor memory and reduced mod 2
  *   GF2_OPT_TC_UPDATE  the PLE / RREF trailing updates on the tensor cores
  *                      instead of the Four-Russians tables
  *   GF2_OPT_TMA_UPDATE the table updates move their rows between HBM and
