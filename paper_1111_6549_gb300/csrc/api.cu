@@ -439,14 +439,13 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
                 if (rc) return rc;
             }
         }
-        r0 = r1;
-        if (r1 >= m) break;                              // no row left to pivot on
-    }
+        r0 = r1;                                         // later blocks still run: their stripe records
+    }                                                    // (rank 0 once no row is left) feed the RREF
     return GF2_OK;
 }
 
 // Enqueue the RREF recovery of a matrix that run_ple just decomposed.
-int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv)
+int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv, const int64_t *Qs)
 {
     const Layout L = layout_for(m, ncols);
     StripeDesc *descs = reinterpret_cast<StripeDesc *>(h->ws + L.descs);
@@ -458,10 +457,15 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         CK(launch_rref_lclear(h->stream, A, m, W, ld, r_dev(h), h->num_sms));
     }
     h->launches += 1;
-    for (int64_t s = ns - 1; s >= 0; --s) {
+    // one stripe's back-substitution: rows [row_lo, r_s) over the words
+    // [c_s, W) except [skip_lo, skip_hi), where those rows and the stripe's
+    // pivot rows are known to be zero
+    auto stripe = [&](int64_t s, int64_t row_lo, int64_t skip_lo, int64_t skip_hi) -> int {
+        const bool split = skip_lo < skip_hi;
         {
             Timed t(h, K_RPREP);
-            CK(launch_rref_prep(h->stream, A, ld, W, (int)s, descs, IDX, m, h->num_sms));
+            CK(launch_rref_prep(h->stream, A, ld, split && skip_hi >= W ? skip_lo : W, (int)s, descs, IDX, m,
+                                h->num_sms));
         }
         h->launches += 1;
         UpdArgs a{};
@@ -472,13 +476,68 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         a.A = A;
         a.ld = ld;
         a.m = m;
-        a.W = W;
+        a.W = split ? skip_lo : W;
+        a.row_lo = row_lo;
         a.desc = descs + s;
         a.stripe = (int)s;
         a.idx = IDX;
         a.idx_stride = 1;
         a.bytes = bytes_dev(h);
         int rc = launch_update_counted(h, a);
+        if (rc || !split || skip_hi >= W) return rc;
+        a.W = W;
+        a.w_lo = skip_hi;
+        return launch_update_counted(h, a);
+    };
+    // Blocked form, whenever the PLE is blocked (explicit width, or the
+    // automatic rule from 65536 pivot columns on): the stripes of the right
+    // half reduce its pivot block [rR, r) among its own rows; the rows above
+    // get the whole block at once -- rows[0:rR] ^= X G, X their bits on the
+    // block's pivot columns, G the reduced block rows, through gf2_mul -- and
+    // are zero on those columns afterwards; the left half's stripes then skip
+    // the words from the block's first column up to its first non-pivot column.
+    const int64_t sR = (ns + 1) / 2;
+    const bool blocked = h->ple_block > 0 ? ns > h->ple_block / 64 : (h->ple_block < 0 && npiv >= 65536);
+    if (blocked && sR < ns) {
+        int64_t rR = 0, r = 0;
+        CK(cudaMemcpyAsync(&rR, &descs[sR].r, sizeof(rR), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&r, r_dev(h), sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const int64_t kb = r - rR;
+        if (kb > 0 && rR > 0) {
+            // the block's pivot columns, for the first column that is not one
+            std::vector<int64_t> qb((size_t)kb);
+            CK(cudaMemcpyAsync(qb.data(), Qs + rR, (size_t)kb * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                               h->stream));
+            for (int64_t s = ns - 1; s >= sR; --s) {
+                int rc = stripe(s, rR, W, W);
+                if (rc) return rc;
+            }
+            const int64_t kw = words_for(kb);
+            int rc = grow(&h->lbuf, &h->lbuf_cap, (size_t)rR * kw * 8, h->stream);
+            if (rc) return rc;
+            uint64_t *X = reinterpret_cast<uint64_t *>(h->lbuf);
+            {
+                Timed t(h, K_OTHER);
+                CK(launch_gather_pivbits(h->stream, A, ld, W, 0, rR, Qs + rR, kb, kw, X, h->num_sms));
+            }
+            h->launches += 1;
+            rc = gf2_mul(h, A + sR, ld, X, kw, A + rR * ld + sR, ld, rR, kb, ncols - 64 * sR, 1);
+            if (rc) return rc;
+            CK(cudaStreamSynchronize(h->stream));   // qb has arrived (ordered before the product)
+            int64_t j = 0;
+            while (j < kb && qb[(size_t)j] == 64 * sR + j) ++j;
+            const int64_t first_free = 64 * sR + j;  // first column of the block that is no pivot
+            const int64_t skip_hi = first_free >= ncols ? W : first_free >> 6;
+            for (int64_t s = sR - 1; s >= 0; --s) {
+                rc = stripe(s, 0, sR, skip_hi);
+                if (rc) return rc;
+            }
+            return GF2_OK;
+        }
+    }
+    for (int64_t s = ns - 1; s >= 0; --s) {
+        int rc = stripe(s, 0, W, W);
         if (rc) return rc;
     }
     return GF2_OK;
@@ -706,7 +765,7 @@ static int rref_enqueue(gf2_handle *h, uint64_t *A, int64_t m, int64_t n, int64_
     int64_t *P = reinterpret_cast<int64_t *>(h->ws + L.P);
     rc = run_ple(h, A, m, n, ld, n, P, Q);
     if (rc) return rc;
-    return run_rref_back(h, A, m, n, ld, n);
+    return run_rref_back(h, A, m, n, ld, n, Q);
 }
 
 int gf2_rref(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64_t *Q, int64_t *rank)
@@ -904,7 +963,7 @@ static int solve_enqueue(gf2_handle *h, uint64_t *A, int64_t n, int64_t lda, uin
     CK(cudaMemsetAsync(flag_dev(h), 0, 4, h->stream));
     CK(launch_solve_check(h->stream, Aug, ldaug, n, wa, wb, r_dev(h), flag_dev(h)));
     h->launches += 1;
-    rc = run_rref_back(h, Aug, n, ncols, ldaug, n);
+    rc = run_rref_back(h, Aug, n, ncols, ldaug, n, Q);
     if (rc) return rc;
     if (nrhs > 0) {
         CK(launch_solve_finish(h->stream, Aug, ldaug, n, wa, words_for(nrhs), r_dev(h), Q, B, ldb));

@@ -97,7 +97,7 @@ struct UpdArgs {
     const uint64_t *B;         // MUL: generator rows B + g * ldb; M4RI: the reduced pivot rows
     int64_t ldb;
     int64_t gen_count;         // MUL: number of generator rows (<= 64)
-    int64_t row_lo, row_hi;    // MUL: rows to update
+    int64_t row_lo, row_hi;    // MUL: rows to update; RREF: row_lo = first row updated (rows end at the block)
     int64_t w_lo;              // MUL: first word to update
     unsigned long long *bytes; // algorithmic bytes counter (may be null)
     int64_t tp_lo, tp_hi;      // tile pairs [tp_lo, tp_hi) of the column range (tp_hi < 0: all)
@@ -158,6 +158,9 @@ int gemm_fp8_counts(void *g, cudaStream_t st, const uint8_t *A8, const uint8_t *
 // blocked PLE (kernels_blocked.cu)
 cudaError_t launch_gather_lbits(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int64_t row0, int64_t rows,
                                 int64_t c0, int64_t kb, int64_t kw, uint64_t *out, int num_sms);
+cudaError_t launch_gather_pivbits(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int64_t row0,
+                                  int64_t rows, const int64_t *Qb, int64_t kb, int64_t kw, uint64_t *out,
+                                  int num_sms);
 cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *descs, int s0,
                                     int s1, int64_t w_lo, int64_t W);
 cudaError_t launch_trsm_diag(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int nt, const uint64_t *Lt,

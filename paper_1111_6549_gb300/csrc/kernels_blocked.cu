@@ -48,6 +48,49 @@ cudaError_t launch_gather_lbits(cudaStream_t st, const uint64_t *A, int64_t ld, 
     return cudaGetLastError();
 }
 
+// out[i][w] = the bits of row row0 + i at the columns Qb[64 w .. 64 w + 64)
+// (bit b of word w from column Qb[64 w + b]) for the first kb entries of the
+// increasing column list Qb (i < rows, w < kw).  A word whose 64 columns are
+// consecutive is one shifted load; the others go bit by bit.
+__global__ void gather_pivbits_kernel(const uint64_t *__restrict__ A, int64_t ld, int64_t W, int64_t row0,
+                                      int64_t rows, const int64_t *__restrict__ Qb, int64_t kb, int64_t kw,
+                                      uint64_t *__restrict__ out)
+{
+    const int64_t total = rows * kw;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / kw, w = t - i * kw;
+        const uint64_t *row = A + (row0 + i) * ld;
+        const int64_t nb = kb - 64 * w < 64 ? kb - 64 * w : 64;
+        const int64_t qf = __ldg(Qb + 64 * w), ql = __ldg(Qb + 64 * w + nb - 1);
+        uint64_t v = 0;
+        if (ql - qf == nb - 1) {
+            const int64_t q = qf >> 6;
+            const int off = (int)(qf & 63);
+            v = row[q] >> off;
+            if (off && q + 1 < W) v |= row[q + 1] << (64 - off);
+            if (nb < 64) v &= (1ull << nb) - 1ull;
+        } else {
+            for (int b = 0; b < nb; ++b) {
+                const int64_t c = __ldg(Qb + 64 * w + b);
+                v |= ((row[c >> 6] >> (c & 63)) & 1ull) << b;
+            }
+        }
+        out[i * kw + w] = v;
+    }
+}
+
+cudaError_t launch_gather_pivbits(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int64_t row0,
+                                  int64_t rows, const int64_t *Qb, int64_t kb, int64_t kw, uint64_t *out,
+                                  int num_sms)
+{
+    int64_t blocks = (rows * kw + 255) / 256;
+    if (blocks > 8 * num_sms) blocks = 8 * num_sms;
+    if (blocks < 1) blocks = 1;
+    gather_pivbits_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, W, row0, rows, Qb, kb, kw, out);
+    return cudaGetLastError();
+}
+
 constexpr int TRSM_THREADS = 256;
 
 // Rows X[0 .. nt) (X = A + row0 * ld) <- Linv X over the words [w_lo, W),

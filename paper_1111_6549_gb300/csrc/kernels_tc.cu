@@ -175,9 +175,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_update_kernel(UpdArgs a)
     } else if (a.mode == UPD_RREF) {
         const int rbar = d->rbar;
         if (rbar == 0) return;
-        row_lo = 0;
+        row_lo = a.row_lo;                    // 0, or the first row of a block's own RREF
         row_hi = d->r;
-        w_lo = d->c >> 6;
+        w_lo = max((int64_t)(d->c >> 6), a.w_lo);  // a.w_lo > 0: only a right part of the row
         if (tid < KS) sGen[tid] = nullptr;
         __syncthreads();
         if (tid < rbar) sGen[d->qbar[tid]] = a.A + (d->r + tid) * a.ld;

@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
     } else if (a.mode == UPD_RREF) {
         const int rbar = d->rbar;
         if (rbar == 0) return;
-        row_lo = 0;
+        row_lo = a.row_lo;                    // 0, or the first row of a block's own RREF
         row_hi = d->r;
-        w_lo = d->c >> 6;
+        w_lo = max((int64_t)(d->c >> 6), a.w_lo);  // a.w_lo > 0: only a right part of the row
         if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
         __syncthreads();
         if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;
@@ -240,9 +240,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     } else if (a.mode == UPD_RREF) {
         const int rbar = d->rbar;
         if (rbar == 0) return;
-        row_lo = 0;
+        row_lo = a.row_lo;                    // 0, or the first row of a block's own RREF
         row_hi = d->r;
-        w_lo = d->c >> 6;
+        w_lo = max((int64_t)(d->c >> 6), a.w_lo);  // a.w_lo > 0: only a right part of the row
         if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
         __syncthreads();
         if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;

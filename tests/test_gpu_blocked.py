@@ -68,3 +68,40 @@ def test_blocked_rref_and_solve():
     assert st == st0
     if st0 != oracle.SOLVE_INCONSISTENT:
         assert np.array_equal(to_host(dB, gi.words_for(nrhs)), B0)
+
+
+@pytest.mark.parametrize("m,n", [(700, 1500), (1500, 700), (640, 640)])
+def test_blocked_rref_wide_tall_and_exhausted(m, n):
+    """Rank reaching m before the last block (wide), tall, and square: the RREF
+    built on the blocked PLE's stripe records."""
+    h = handle(128, 1)
+    A = make("dense", m, n, seed=m + 3 * n)
+    dR = to_dev(A)
+    Q = vec_dev(min(m, n))
+    r = h.rref(dR, m, n, Q)
+    R0 = A.copy()
+    r0, Q0 = oracle.rref(R0, m, n)
+    assert r == r0 and np.array_equal(Q.cpu().numpy()[:min(m, n)], Q0)
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+
+
+@pytest.mark.parametrize("dups", [(), (700,), (640,), (767, 768), (900, 1000, 1270, 1279), (1279,)])
+def test_blocked_rref_pivot_gaps(dups):
+    """The right half's pivot columns with gaps (a column equal to an earlier
+    one is no pivot): the gathered bits then come from scattered columns, and
+    the left stripes skip only the words before the first gap."""
+    m = n = 1280
+    A = make("dense", m, n, seed=sum(dups) + 11)
+    U = gi.unpack(A, m, n)
+    for c in dups:
+        U[:, c] = U[:, c - 37]
+    A = gi.pack(U, A.shape[1])
+    h = handle(640, 1)
+    dR = to_dev(A)
+    Q = vec_dev(n)
+    r = h.rref(dR, m, n, Q)
+    R0 = A.copy()
+    r0, Q0 = oracle.rref(R0, m, n)
+    assert r == r0 and np.array_equal(Q.cpu().numpy()[:r0], Q0[:r0])
+    assert not set(dups) & set(Q0[:r0].tolist())
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
