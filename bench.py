@@ -419,17 +419,21 @@ def tc_compare(args):
         B = torch.from_numpy(gi.bernoulli_matrix(k, n, 2).view(np.int64)).to(dev)
         C = torch.zeros((m, gi.words_for(n)), dtype=torch.int64, device=dev)
         res, outs = {"m": m, "k": k, "n": n}, {}
-        for name, tc, gk in (("table", 0, 0), ("tcgen05", 1, 0), ("fp8_gemm", 0, 1)):
+        for name, tc, gk, fmt in (("table", 0, 0, 8), ("tcgen05", 1, 0, 8), ("fp8_gemm", 0, 1, 8),
+                                  ("fp4_gemm", 0, 1, 4)):
             h.set_option(g.OPT_TC_MUL, tc)
             h.set_option(g.OPT_MUL_GEMM_MIN_K, gk)
+            h.set_option(g.OPT_MUL_GEMM_FORMAT, fmt)
             res[name + "_ms"] = timeit(lambda: h.mul(C, A, B, m, k, n))
             res[name + "_tera_and_xor_per_s"] = m * k * n / (res[name + "_ms"] / 1e3) / 1e12
             outs[name] = C.clone()
         res["identical"] = bool(torch.equal(outs["table"], outs["tcgen05"]) and
-                                torch.equal(outs["table"], outs["fp8_gemm"]))
+                                torch.equal(outs["table"], outs["fp8_gemm"]) and
+                                torch.equal(outs["table"], outs["fp4_gemm"]))
         out["mul"].append(res)
     h.set_option(g.OPT_TC_MUL, 0)
     h.set_option(g.OPT_MUL_GEMM_MIN_K, 4096)
+    h.set_option(g.OPT_MUL_GEMM_FORMAT, 4)
     for nn in (16384, 32768):
         A = torch.from_numpy(gi.dense_square(nn).view(np.int64)).to(dev)
         Wk = torch.empty_like(A)
@@ -470,6 +474,8 @@ def run_ours(args):
         h.set_option(g.OPT_TMA_UPDATE, 1)
     if args.ple_block is not None:
         h.set_option(g.OPT_PLE_BLOCK, args.ple_block)
+    if args.gemm_format is not None:
+        h.set_option(g.OPT_MUL_GEMM_FORMAT, args.gemm_format)
     stream = torch.cuda.current_stream(dev)
 
     m = n = args.n
@@ -713,6 +719,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--gemm-format", type=int, default=None, choices=(8, 4),
+                    help="operand format of the library GEMM in the blocked products (default: the library's)")
     ap.add_argument("--ple-block", type=int, default=None,
                     help="PLE column block for the blocked trailing update (GF2_OPT_PLE_BLOCK)")
     ap.add_argument("--tma", action="store_true",

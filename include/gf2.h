@@ -122,9 +122,9 @@ int gf2_rref_m4ri_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, 
  *   C must not overlap A or B.  Asynchronous.
  * Inner dimensions below GF2_OPT_MUL_GEMM_MIN_K (default 4096) use the
  * tabulated row combinations, 64 columns of A per pass over C; larger ones
- * the exact FP8 GEMM (see the options); GF2_OPT_TC_MUL selects the library's
- * own tcgen05 kernel instead.  The FP8 GEMM path holds up to about 1 GiB of
- * fp32 counts plus the expanded operands in the handle's workspace.
+ * the exact FP4 (or FP8) GEMM (see the options); GF2_OPT_TC_MUL selects the
+ * library's own tcgen05 kernel instead.  The GEMM path holds up to about
+ * 1 GiB of fp32 counts plus the expanded operands in the handle's workspace.
  */
 int gf2_mul(gf2_handle_t handle, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda,
             const uint64_t *B, int64_t ldb, int64_t m, int64_t k, int64_t n, int accumulate);
@@ -305,10 +305,11 @@ int gf2_server_destroy(gf2_server_t server);
  *                      where the matrix allows it (16-byte aligned base, even
  *                      ld_words, at least 16 words and 256 rows)
  *   GF2_OPT_MUL_GEMM_MIN_K  gf2_mul with an inner dimension k >= value (0:
- *                      never) runs as an exact FP8 GEMM: the library's own
- *                      kernels expand the bits to FP8 0/1, a plain cuBLASLt
- *                      FP8 GEMM counts, and the library takes the parities;
- *                      below it, the Four-Russians tables (default 4096)
+ *                      never) runs as an exact low-precision GEMM: the
+ *                      library's own kernels expand the bits to FP4 (or FP8)
+ *                      0/1, a plain cuBLASLt GEMM counts in fp32, and the
+ *                      library takes the parities; below it, the
+ *                      Four-Russians tables (default 4096)
  *   GF2_OPT_PLE_BLOCK  value > 0 (a multiple of 64): PLE (and everything
  *                      built on it) decomposes value columns at a time with
  *                      the updates inside the block, then applies the
@@ -320,10 +321,15 @@ int gf2_server_destroy(gf2_server_t server);
  *                      0: one table update per 64-column stripe; -1
  *                      (default): blocks of half the pivot columns from
  *                      65536 pivot columns on, else 0
+ *   GF2_OPT_MUL_GEMM_FORMAT  operand format of that GEMM: 4 = FP4 E2M1
+ *                      with every 16-value block scale 1.0 (NVFP4 form, the
+ *                      FP4 tensor rate; default), 8 = FP8 E4M3; the counts
+ *                      are exact either way
  * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
- * GF2_EINVAL for an unknown option or a negative value.
+ * GF2_EINVAL for an unknown option, a negative value, or a format other
+ * than 8 or 4.
  */
 #define GF2_OPT_LOOKAHEAD       1
 #define GF2_OPT_TC_MUL          2
@@ -331,6 +337,7 @@ int gf2_server_destroy(gf2_server_t server);
 #define GF2_OPT_TMA_UPDATE      4
 #define GF2_OPT_MUL_GEMM_MIN_K  5
 #define GF2_OPT_PLE_BLOCK       6
+#define GF2_OPT_MUL_GEMM_FORMAT 7
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */

@@ -45,12 +45,13 @@ struct gf2_handle {
     double kind_ms[5] = {0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other
     BatchTune btune{};             // batched kernel: table configuration per size class
     bool tma = false;              // update rows move by TMA where A allows it (measured slower)
-    int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the FP8 GEMM
+    int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the library GEMM
+    int gemm_fmt = 4;              // its operand format: 4 = FP4 E2M1 (block scales 1), 8 = FP8 E4M3
     int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
     char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
     size_t lbuf_cap = 0;
     void *lt = nullptr;            // cuBLASLt state (created on first use)
-    char *gbuf = nullptr;          // FP8 operands and fp32 counts of the GEMM path
+    char *gbuf = nullptr;          // expanded operands and fp32 counts of the GEMM path
     size_t gbuf_cap = 0;
     TensorMap2D tmap{};            // TMA descriptor of the last updated matrix
     const void *tm_A = nullptr;
@@ -389,7 +390,7 @@ static int trsm_lower(gf2_handle *h, uint64_t *A, int64_t ld, int64_t row0, int6
 // updates restricted to the block, and the columns right of each block get
 // the block's whole trailing update at once: the TRSM U = L11^-1 A12 on the
 // block's pivot rows (one 64 x 64 diagonal inverse plus one table pass per
-// 64 pivots) and A22 ^= L21 U through gf2_mul (the FP8 GEMM for large
+// 64 pivots) and A22 ^= L21 U through gf2_mul (the FP4 GEMM for large
 // blocks).  The host reads the rank once per block.
 int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv, int64_t *P,
             int64_t *Q)
@@ -832,9 +833,11 @@ int gf2_rref_m4ri_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64
     return GF2_OK;
 }
 
-// C ^= A B through the FP8 GEMM (kernels_gemm.cu): B is expanded once per
+// C ^= A B through the library GEMM (kernels_gemm.cu): B is expanded once per
 // chunk of at most 2^22 rows (fp32 counts stay exact and below 2^23), A and
-// the fp32 counts in row blocks of about 1 GiB of counts.
+// the fp32 counts in row blocks of about 1 GiB of counts.  The FP4 GEMM takes
+// only sizes that are multiples of 16, so in that format both operands get
+// zero rows up to the next multiple of 16 (their counts are never read).
 static int mul_gemm(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
                     int64_t ldb, int64_t m, int64_t k, int64_t n)
 {
@@ -850,7 +853,10 @@ static int mul_gemm(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, 
         int64_t mb = std::max<int64_t>(1, (int64_t(1) << 30) / (ldd * 4));
         mb = std::min(mb, m);
         mb = (mb + 15) & ~int64_t(15);
-        const size_t bbytes = align256((size_t)n * kp), abytes = align256((size_t)mb * kp),
+        const int fmt = h->gemm_fmt;
+        const int64_t np = fmt == 4 ? ldd : n;           // operand rows of B^T handed to the GEMM
+        const size_t rowb = (size_t)kp * fmt / 8;        // bytes of one expanded row
+        const size_t bbytes = align256((size_t)np * rowb), abytes = align256((size_t)mb * rowb),
                      dbytes = align256((size_t)mb * ldd * 4);
         int rc = grow(&h->gbuf, &h->gbuf_cap, bbytes + abytes + dbytes, h->stream);
         if (rc) return rc;
@@ -859,18 +865,22 @@ static int mul_gemm(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, 
         float *D = reinterpret_cast<float *>(h->gbuf + bbytes + abytes);
         {
             Timed t(h, K_OTHER);
-            CK(launch_expand_transpose(h->stream, B + k0 * ldb, ldb, 0, kc, n, kp, B8t, h->num_sms));
+            CK(launch_expand_transpose(h->stream, fmt, B + k0 * ldb, ldb, 0, kc, n, kp, B8t, h->num_sms));
         }
         h->launches += 1;
+        if (np > n) CK(cudaMemsetAsync(B8t + (size_t)n * rowb, 0, (size_t)(np - n) * rowb, h->stream));
         for (int64_t i0 = 0; i0 < m; i0 += mb) {
             const int64_t rows = std::min(mb, m - i0);
             {
                 Timed t(h, K_OTHER);
-                CK(launch_expand_rows(h->stream, A + i0 * lda, lda, rows, k0, k0 + kc, kp, A8, h->num_sms));
+                CK(launch_expand_rows(h->stream, fmt, A + i0 * lda, lda, rows, k0, k0 + kc, kp, A8, h->num_sms));
             }
+            const int64_t rows_p = fmt == 4 ? (rows + 15) & ~int64_t(15) : rows;   // <= mb
+            if (rows_p > rows)
+                CK(cudaMemsetAsync(A8 + (size_t)rows * rowb, 0, (size_t)(rows_p - rows) * rowb, h->stream));
             {
                 Timed t(h, K_OTHER);
-                if (gemm_fp8_counts(h->lt, h->stream, A8, B8t, D, rows, n, kp, ldd) != 0) return GF2_ECUDA;
+                if (gemm_counts(h->lt, h->stream, fmt, A8, B8t, D, rows_p, np, kp, ldd) != 0) return GF2_ECUDA;
             }
             {
                 Timed t(h, K_OTHER);
@@ -1398,6 +1408,10 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
     case GF2_OPT_PLE_BLOCK:
         if (value < -1 || (value > 0 && value % 64)) return GF2_EINVAL;
         h->ple_block = value;
+        return GF2_OK;
+    case GF2_OPT_MUL_GEMM_FORMAT:
+        if (value != 8 && value != 4) return GF2_EINVAL;
+        h->gemm_fmt = (int)value;
         return GF2_OK;
     case GF2_OPT_MUL_GEMM_MIN_K:
         if (value < 0) return GF2_EINVAL;

@@ -144,17 +144,17 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
-// GF(2) product through an FP8 GEMM (kernels_gemm.cu)
-cudaError_t launch_expand_rows(cudaStream_t st, const uint64_t *A, int64_t lda, int64_t rows, int64_t k0, int64_t k,
-                               int64_t kp, uint8_t *out, int num_sms);
-cudaError_t launch_expand_transpose(cudaStream_t st, const uint64_t *B, int64_t ldb, int64_t k0, int64_t k, int64_t n,
-                                    int64_t kp, uint8_t *out, int num_sms);
+// GF(2) product through a library FP4 / FP8 GEMM (kernels_gemm.cu)
+cudaError_t launch_expand_rows(cudaStream_t st, int fmt, const uint64_t *A, int64_t lda, int64_t rows, int64_t k0,
+                               int64_t k, int64_t kp, uint8_t *out, int num_sms);
+cudaError_t launch_expand_transpose(cudaStream_t st, int fmt, const uint64_t *B, int64_t ldb, int64_t k0, int64_t k,
+                                    int64_t n, int64_t kp, uint8_t *out, int num_sms);
 cudaError_t launch_parity(cudaStream_t st, const float *D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,
                           int64_t ldc, int num_sms);
 void *gemm_lt_create();
 void gemm_lt_destroy(void *g);
-int gemm_fp8_counts(void *g, cudaStream_t st, const uint8_t *A8, const uint8_t *B8t, float *D, int64_t rows,
-                    int64_t n, int64_t kp, int64_t ldd);
+int gemm_counts(void *g, cudaStream_t st, int fmt, const uint8_t *Ax, const uint8_t *Bxt, float *D, int64_t rows,
+                int64_t n, int64_t kp, int64_t ldd);
 // blocked PLE (kernels_blocked.cu)
 cudaError_t launch_gather_lbits(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int64_t row0, int64_t rows,
                                 int64_t c0, int64_t kb, int64_t kw, uint64_t *out, int num_sms);

@@ -14,10 +14,11 @@ from tests.test_gpu_parity import assert_ple_equal, make, ref_ple
 pytestmark = pytest.mark.gpu
 
 
-def handle(block, gemm_min_k=None):
+def handle(block, gemm_min_k=None, fmt=8):
     import paper_1111_6549_gb300 as g
     h = g.Handle()
     h.set_option(g.OPT_PLE_BLOCK, block)
+    h.set_option(g.OPT_MUL_GEMM_FORMAT, fmt)
     if gemm_min_k is not None:
         h.set_option(g.OPT_MUL_GEMM_MIN_K, gemm_min_k)
     return h
@@ -40,12 +41,12 @@ def test_blocked_ple_matches_oracle(block, kind, m, n):
     assert_ple_equal(run(handle(block), A, m, n), ref_ple(A, m, n))
 
 
-@pytest.mark.parametrize("gemm_min_k", [1, 0])
-def test_blocked_ple_gemm_and_table_products(gemm_min_k):
-    """The block's product through the FP8 GEMM (min k 1) and through the tables (0)."""
+@pytest.mark.parametrize("gemm_min_k,fmt", [(1, 8), (1, 4), (0, 8)])
+def test_blocked_ple_gemm_and_table_products(gemm_min_k, fmt):
+    """The block's product through the FP8 or FP4 GEMM (min k 1) and through the tables (0)."""
     m, n = 3000, 2049
     A = make("dense", m, n, seed=3)
-    assert_ple_equal(run(handle(512, gemm_min_k), A, m, n, ld_extra=1), ref_ple(A, m, n))
+    assert_ple_equal(run(handle(512, gemm_min_k, fmt), A, m, n, ld_extra=1), ref_ple(A, m, n))
 
 
 def test_blocked_rref_and_solve():
@@ -96,7 +97,7 @@ def test_blocked_rref_pivot_gaps(dups):
     for c in dups:
         U[:, c] = U[:, c - 37]
     A = gi.pack(U, A.shape[1])
-    h = handle(640, 1)
+    h = handle(640, 1, 4 if len(dups) % 2 else 8)
     dR = to_dev(A)
     Q = vec_dev(n)
     r = h.rref(dR, m, n, Q)

@@ -98,7 +98,7 @@ def test_sparse_square_32768(h):
 
 @pytest.mark.parametrize("block", [8192, 16384])
 def test_dense_square_blocked_fullsize(h, block):
-    """The blocked PLE (block trailing updates through the FP8 GEMM) at 65536^2."""
+    """The blocked PLE (block trailing updates through the library GEMM) at 65536^2."""
     A = gi.dense_square(65536)
     r = ple_and_rref_checked(h, A, 65536, 65536, block=block)
     assert 65536 - 8 <= r <= 65536

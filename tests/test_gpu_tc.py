@@ -92,11 +92,14 @@ def test_tma_update_ple_rref_and_mul(m, n):
 @pytest.mark.parametrize("m,k,n", [(1, 1, 1), (128, 64, 256), (300, 70, 300), (129, 65, 257), (1000, 5000, 1000),
                                    (513, 4099, 300), (2048, 130, 4100), (64, 0, 64)])
 @pytest.mark.parametrize("accumulate", [False, True])
-def test_mul_through_fp8_gemm(m, k, n, accumulate):
-    """gf2_mul through the exact FP8 GEMM (forced for every k)."""
+@pytest.mark.parametrize("fmt", [8, 4])
+def test_mul_through_library_gemm(m, k, n, accumulate, fmt):
+    """gf2_mul through the exact library GEMM (forced for every k), with FP8
+    E4M3 operands and with block-scaled FP4 E2M1 operands."""
     import paper_1111_6549_gb300 as g
     hh = g.Handle()
     hh.set_option(g.OPT_MUL_GEMM_MIN_K, 1)
+    hh.set_option(g.OPT_MUL_GEMM_FORMAT, fmt)
     A = gi.bernoulli_matrix(m, k, 21) if k else np.zeros((m, 1), np.uint64)
     B = gi.bernoulli_matrix(k, n, 22) if k else np.zeros((1, gi.words_for(n)), np.uint64)
     C0 = gi.bernoulli_matrix(m, n, 23)
@@ -109,7 +112,7 @@ def test_mul_through_fp8_gemm(m, k, n, accumulate):
 
 
 def test_mul_default_large_k_matches_oracle():
-    """Default options: a large inner dimension takes the FP8 GEMM path."""
+    """Default options: a large inner dimension takes the library GEMM path (FP4 operands)."""
     import paper_1111_6549_gb300 as g
     hh = g.Handle()
     m, k, n = 700, 9000, 1100
