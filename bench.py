@@ -476,6 +476,8 @@ def run_ours(args):
         h.set_option(g.OPT_PLE_BLOCK, args.ple_block)
     if args.gemm_format is not None:
         h.set_option(g.OPT_MUL_GEMM_FORMAT, args.gemm_format)
+    if args.rref_block is not None:
+        h.set_option(g.OPT_RREF_BLOCK, args.rref_block)
     stream = torch.cuda.current_stream(dev)
 
     m = n = args.n
@@ -721,6 +723,8 @@ def main():
     ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--gemm-format", type=int, default=None, choices=(8, 4),
                     help="operand format of the library GEMM in the blocked products (default: the library's)")
+    ap.add_argument("--rref-block", type=int, default=None,
+                    help="base block width of the recursive RREF recovery (0: flat; default: the library's)")
     ap.add_argument("--ple-block", type=int, default=None,
                     help="PLE column block for the blocked trailing update (GF2_OPT_PLE_BLOCK)")
     ap.add_argument("--tma", action="store_true",

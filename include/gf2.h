@@ -325,6 +325,16 @@ int gf2_server_destroy(gf2_server_t server);
  *                      with every 16-value block scale 1.0 (NVFP4 form, the
  *                      FP4 tensor rate; default), 8 = FP8 E4M3; the counts
  *                      are exact either way
+ *   GF2_OPT_RREF_BLOCK value > 0 (a multiple of 64): the RREF recovery
+ *                      (gf2_rref, gf2_solve) halves the pivot stripes
+ *                      recursively down to blocks of value columns: the
+ *                      right half is reduced on its own rows, the rows of the
+ *                      left half are cleared on its pivot columns by one
+ *                      product through gf2_mul, then the left half follows;
+ *                      the table passes run only inside the blocks.  0: one
+ *                      table pass per stripe over all rows above it; -1
+ *                      (default): blocks of 16384 columns from 65536 pivot
+ *                      columns on, else 0
  * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
@@ -338,6 +348,7 @@ int gf2_server_destroy(gf2_server_t server);
 #define GF2_OPT_MUL_GEMM_MIN_K  5
 #define GF2_OPT_PLE_BLOCK       6
 #define GF2_OPT_MUL_GEMM_FORMAT 7
+#define GF2_OPT_RREF_BLOCK      8
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <utility>
 #include <vector>
@@ -47,6 +48,7 @@ struct gf2_handle {
     bool tma = false;              // update rows move by TMA where A allows it (measured slower)
     int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the library GEMM
     int gemm_fmt = 4;              // its operand format: 4 = FP4 E2M1 (block scales 1), 8 = FP8 E4M3
+    int64_t rref_block = -1;       // RREF recovery: base block width of the recursive form (0: flat, -1: auto)
     int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
     char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
     size_t lbuf_cap = 0;
@@ -490,52 +492,77 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         a.w_lo = skip_hi;
         return launch_update_counted(h, a);
     };
-    // Blocked form, whenever the PLE is blocked (explicit width, or the
-    // automatic rule from 65536 pivot columns on): the stripes of the right
-    // half reduce its pivot block [rR, r) among its own rows; the rows above
-    // get the whole block at once -- rows[0:rR] ^= X G, X their bits on the
-    // block's pivot columns, G the reduced block rows, through gf2_mul -- and
-    // are zero on those columns afterwards; the left half's stripes then skip
-    // the words from the block's first column up to its first non-pivot column.
-    const int64_t sR = (ns + 1) / 2;
-    const bool blocked = h->ple_block > 0 ? ns > h->ple_block / 64 : (h->ple_block < 0 && npiv >= 65536);
-    if (blocked && sR < ns) {
-        int64_t rR = 0, r = 0;
-        CK(cudaMemcpyAsync(&rR, &descs[sR].r, sizeof(rR), cudaMemcpyDeviceToHost, h->stream));
+    // Blocked form (recursive halving down to blocks of rref_base stripes).
+    // Invariant of a call on the stripes [a, b): their pivot rows [r_a, r_b)
+    // are already zero on every pivot column of the stripes >= b.  The call
+    // reduces the right half [mid, b) on its own rows, clears the left half's
+    // rows [r_a, r_mid) on the right half's pivot columns at once --
+    // rows ^= X G, X their bits on those columns, G the reduced right rows,
+    // through gf2_mul -- and recurses into the left half.  Table passes and
+    // products skip the words from stripe b's first column up to the first
+    // column at or after it that is no pivot: zero in every row involved.
+    const int64_t base = h->rref_block > 0 ? h->rref_block / 64
+                                           : (h->rref_block < 0 && npiv >= 65536 ? 256 : 0);
+    if (base > 0 && ns > base) {
+        int64_t r = 0;
         CK(cudaMemcpyAsync(&r, r_dev(h), sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+        std::vector<int64_t> rs((size_t)ns + 1);
+        CK(cudaMemcpy2DAsync(rs.data(), sizeof(int64_t), &descs[0].r, sizeof(StripeDesc), sizeof(int64_t),
+                             (size_t)ns, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
-        const int64_t kb = r - rR;
-        if (kb > 0 && rR > 0) {
-            // the block's pivot columns, for the first column that is not one
-            std::vector<int64_t> qb((size_t)kb);
-            CK(cudaMemcpyAsync(qb.data(), Qs + rR, (size_t)kb * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                               h->stream));
-            for (int64_t s = ns - 1; s >= sR; --s) {
-                int rc = stripe(s, rR, W, W);
-                if (rc) return rc;
-            }
-            const int64_t kw = words_for(kb);
-            int rc = grow(&h->lbuf, &h->lbuf_cap, (size_t)rR * kw * 8, h->stream);
-            if (rc) return rc;
-            uint64_t *X = reinterpret_cast<uint64_t *>(h->lbuf);
-            {
-                Timed t(h, K_OTHER);
-                CK(launch_gather_pivbits(h->stream, A, ld, W, 0, rR, Qs + rR, kb, kw, X, h->num_sms));
-            }
-            h->launches += 1;
-            rc = gf2_mul(h, A + sR, ld, X, kw, A + rR * ld + sR, ld, rR, kb, ncols - 64 * sR, 1);
-            if (rc) return rc;
-            CK(cudaStreamSynchronize(h->stream));   // qb has arrived (ordered before the product)
-            int64_t j = 0;
-            while (j < kb && qb[(size_t)j] == 64 * sR + j) ++j;
-            const int64_t first_free = 64 * sR + j;  // first column of the block that is no pivot
-            const int64_t skip_hi = first_free >= ncols ? W : first_free >> 6;
-            for (int64_t s = sR - 1; s >= 0; --s) {
-                rc = stripe(s, 0, sR, skip_hi);
-                if (rc) return rc;
-            }
-            return GF2_OK;
+        rs[(size_t)ns] = r;
+        std::vector<int64_t> q((size_t)std::max<int64_t>(r, 1));
+        if (r > 0) {
+            CK(cudaMemcpyAsync(q.data(), Qs, (size_t)r * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
         }
+        // first word past stripe b's cleared words: the word of the first
+        // column >= 64 b that is no pivot (W when there is none)
+        auto skip_end = [&](int64_t b) -> int64_t {
+            if (b >= ns) return W;
+            int64_t j = rs[(size_t)b], c = 64 * b;
+            while (j < r && q[(size_t)j] == c) ++j, ++c;
+            return c >= ncols ? W : c >> 6;
+        };
+        std::function<int(int64_t, int64_t)> rec = [&](int64_t a, int64_t b) -> int {
+            const int64_t ra = rs[(size_t)a], rb = rs[(size_t)b];
+            if (rb == ra) return GF2_OK;                     // no pivot rows: nothing to reduce
+            const int64_t sk = skip_end(b);
+            if (b - a <= base) {
+                for (int64_t s = b - 1; s >= a; --s) {
+                    int rc = stripe(s, ra, b < ns ? b : W, sk);
+                    if (rc) return rc;
+                }
+                return GF2_OK;
+            }
+            const int64_t mid = (a + b + 1) / 2;
+            int rc = rec(mid, b);
+            if (rc) return rc;
+            const int64_t rm = rs[(size_t)mid];
+            const int64_t kb = rb - rm, rows = rm - ra;
+            if (kb > 0 && rows > 0) {
+                const int64_t kw = words_for(kb);
+                rc = grow(&h->lbuf, &h->lbuf_cap, (size_t)rows * kw * 8, h->stream);
+                if (rc) return rc;
+                uint64_t *X = reinterpret_cast<uint64_t *>(h->lbuf);
+                {
+                    Timed t(h, K_OTHER);
+                    CK(launch_gather_pivbits(h->stream, A, ld, W, ra, rows, Qs + rm, kb, kw, X, h->num_sms));
+                }
+                h->launches += 1;
+                // G's words [mid, b) and, past the skipped words, [sk, W)
+                const int64_t w_end = b < ns ? b : W;
+                const int64_t n1 = std::min(64 * w_end, ncols) - 64 * mid;
+                rc = gf2_mul(h, A + ra * ld + mid, ld, X, kw, A + rm * ld + mid, ld, rows, kb, n1, 1);
+                if (rc) return rc;
+                if (w_end < W && sk < W) {
+                    rc = gf2_mul(h, A + ra * ld + sk, ld, X, kw, A + rm * ld + sk, ld, rows, kb, ncols - 64 * sk, 1);
+                    if (rc) return rc;
+                }
+            }
+            return rec(a, mid);
+        };
+        return rec(0, ns);
     }
     for (int64_t s = ns - 1; s >= 0; --s) {
         int rc = stripe(s, 0, W, W);
@@ -1408,6 +1435,10 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
     case GF2_OPT_PLE_BLOCK:
         if (value < -1 || (value > 0 && value % 64)) return GF2_EINVAL;
         h->ple_block = value;
+        return GF2_OK;
+    case GF2_OPT_RREF_BLOCK:
+        if (value < -1 || (value > 0 && value % 64)) return GF2_EINVAL;
+        h->rref_block = value;
         return GF2_OK;
     case GF2_OPT_MUL_GEMM_FORMAT:
         if (value != 8 && value != 4) return GF2_EINVAL;

@@ -83,6 +83,7 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
 
     // ---------------- outputs
     const int rbar = sh.rbar;
+    __shared__ uint64_t sMinv[KS], sLinv[KS];          // shared copies for the prep tables
     if (warp == 1) {
         // U11^-1 for the RREF recovery, U11[p][q] = E11[p] at column qbar[q]
         // (unit upper triangular): lane-parallel backward substitution per
@@ -104,10 +105,14 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         for (int p = 0; p < rbar; ++p) {
             const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
             const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
-            if (lane == 0) d->Minv[p] = ((uint64_t)hi << 32) | lo;
+            if (lane == 0) {
+                const uint64_t v = ((uint64_t)hi << 32) | lo;
+                d->Minv[p] = v;
+                sMinv[p] = v;
+            }
         }
     }
-    if (warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv);
+    if (warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv, sLinv);
     for (int p = tid; p < rbar; p += blockDim.x) {
         P[r + p] = r + sh.t[p];
         Q[r + p] = c + sh.j[p];
@@ -134,17 +139,16 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
     // of the word (non-pivot columns select nothing).
     __shared__ uint64_t tMv[KS], tMx[KS], tMg[KS];
     __shared__ int8_t tcolp[KS];
-    __syncthreads();                                   // Minv and Linv are written
     if (tid < KS) tcolp[tid] = -1;
-    __syncthreads();
+    __syncthreads();                                   // Minv and Linv are written
     if (tid < rbar) {
-        const uint64_t mp = d->Minv[tid];
+        const uint64_t mp = sMinv[tid];
         uint64_t x = 0, g = 0;
-        for (int q = 0; q < rbar; ++q)
-            if ((mp >> q) & 1ull) {
-                x ^= d->Linv[q];
-                g ^= sh.E[q];
-            }
+        for (int q = 0; q < rbar; ++q) {
+            const uint64_t sel = 0ull - ((mp >> q) & 1ull);
+            x ^= sLinv[q] & sel;
+            g ^= sh.E[q] & sel;
+        }
         tMv[tid] = mp;
         tMx[tid] = x;
         tMg[tid] = g;

@@ -11,23 +11,6 @@
 
 namespace gf2 {
 
-// Transpose a 32 x 32 bit block held one row per lane (bit c of lane r =
-// entry (r, c)) so that lane c receives column c (bit r = entry (r, c)):
-// five rounds of swapping the off-diagonal sub-blocks of size 16, 8, 4, 2, 1.
-__device__ __forceinline__ unsigned transpose32(unsigned x)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int j = 16 >> k;
-        const unsigned m = masks[k];
-        const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
-        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
-    }
-    return x;
-}
-
 // Shared state of one stripe's pivot search.
 struct PanelShared {
     uint64_t E[KS], L[KS];     // pivot rows' stripe words (echelon) and L coefficients
@@ -45,128 +28,118 @@ struct PanelShared {
     int32_t zpos[KS], zsrc[KS];
 };
 
-// Fast path, called by one whole warp: a bit-sliced window of up to 128 rows
-// (lane l owns columns l and l+32 as 128-row masks).  Sets sh.fail when some
-// column's pivot may lie outside the window; otherwise sh.rbar, E, L, t, j
-// and the staged-row list.
+// One of four registers by a warp-uniform index (no local-memory array).
+template <typename T>
+__device__ __forceinline__ T pick4(const T (&v)[4], int b)
+{
+    return b == 0 ? v[0] : b == 1 ? v[1] : b == 2 ? v[2] : v[3];
+}
+
+// Fast path, called by one whole warp: a window of up to 128 rows held in
+// registers, lane l owning the window slots l, l+32, l+64 and l+96 (their
+// stripe words, their L coefficients -- bit q: eliminated by pivot q -- and
+// the slot their content came from).  A pivot step is four ballots for the
+// slots holding column j, a find-first-set for the pivot slot t, one
+// broadcast of the pivot row (plus an exchange with slot p when t != p) and
+// a conditional XOR per owned slot.  Sets sh.fail when some column's pivot
+// may lie outside the window; otherwise sh.rbar, E, L, t, j and the
+// staged-row list.
 __device__ __forceinline__ void panel_window(const uint64_t *__restrict__ A, int64_t r, int64_t ld,
                                              int64_t cw, int64_t rows, int keff, PanelShared &sh)
 {
     const int lane = threadIdx.x & 31;
-        const int Wn = (int)min(rows, (int64_t)PANEL_WIN);
-        // load: lane l holds window rows l, l+32, l+64, l+96 ...
-        uint64_t rw[4];
+    const unsigned FULL = 0xffffffffu;
+    const int Wn = (int)min(rows, (int64_t)PANEL_WIN);
+    uint64_t R[4], Lc[4];
+    int org[4];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int sl = b * 32 + lane;
-            rw[b] = (sl < Wn) ? A[(r + sl) * ld + cw] : 0ull;
+    for (int b = 0; b < 4; ++b) {
+        const int sl = b * 32 + lane;
+        R[b] = (sl < Wn) ? A[(r + sl) * ld + cw] : 0ull;
+        Lc[b] = 0ull;
+        org[b] = sl;
+    }
+    int p = 0, tmax = -1;
+    bool fail = false;
+    for (int j = 0; j < keff && p < Wn; ++j) {
+        // slots holding column j, from slot p on
+        const unsigned m0 = __ballot_sync(FULL, (unsigned)(R[0] >> j) & 1u);
+        const unsigned m1 = __ballot_sync(FULL, (unsigned)(R[1] >> j) & 1u);
+        const unsigned m2 = __ballot_sync(FULL, (unsigned)(R[2] >> j) & 1u);
+        const unsigned m3 = __ballot_sync(FULL, (unsigned)(R[3] >> j) & 1u);
+        const uint64_t lo = (((uint64_t)m1 << 32) | m0) & ((p < 64) ? (~0ull << p) : 0ull);
+        const uint64_t hi = (((uint64_t)m3 << 32) | m2) & ((p < 64) ? ~0ull : (~0ull << (p - 64)));
+        int t;
+        if (lo) t = __ffsll((long long)lo) - 1;
+        else if (hi) t = 64 + __ffsll((long long)hi) - 1;
+        else {
+            if (Wn < rows) { fail = true; break; }   // the pivot may lie outside the window
+            continue;                                // column j has no pivot
         }
-        // ... transposed so that lane l owns columns l and l+32 as 128-row masks
-        uint64_t c0lo, c0hi, c1lo, c1hi;
-        {
-            unsigned t0[4], t1[4];
+        const int bt = t >> 5, lt = t & 31, bp = p >> 5, lp = p & 31;
+        const uint64_t prow = __shfl_sync(FULL, pick4(R, bt), lt);
+        if (t != p) {
+            // exchange slots p and t: slot p takes the pivot row, slot t the old row p
+            const uint64_t plc = __shfl_sync(FULL, pick4(Lc, bt), lt);
+            const int orgt = __shfl_sync(FULL, pick4(org, bt), lt);
+            const uint64_t rowp = __shfl_sync(FULL, pick4(R, bp), lp);
+            const uint64_t lcp = __shfl_sync(FULL, pick4(Lc, bp), lp);
+            const int orgp = __shfl_sync(FULL, pick4(org, bp), lp);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                t0[b] = transpose32((unsigned)rw[b]);
-                t1[b] = transpose32((unsigned)(rw[b] >> 32));
+                if (b == bp && lane == lp) { R[b] = prow; Lc[b] = plc; org[b] = orgt; }
+                if (b == bt && lane == lt) { R[b] = rowp; Lc[b] = lcp; org[b] = orgp; }
             }
-            c0lo = ((uint64_t)t0[1] << 32) | t0[0];
-            c0hi = ((uint64_t)t0[3] << 32) | t0[2];
-            c1lo = ((uint64_t)t1[1] << 32) | t1[0];
-            c1hi = ((uint64_t)t1[3] << 32) | t1[2];
         }
-        for (int x = lane; x < PANEL_WIN; x += 32) sh.perm[x] = x;
-        __syncwarp();
-        // L columns (pivot p's column = rows eliminated by it), lane owns p = lane, lane + 32
-        uint64_t l0lo = 0, l0hi = 0, l1lo = 0, l1hi = 0;
-        int p = 0, tmax = -1;
-        bool fail = false;
-        for (int j = 0; j < keff && p < Wn; ++j) {
-            const int owner = j & 31;
-            uint64_t jlo = __shfl_sync(0xffffffffu, (j < 32) ? c0lo : c1lo, owner);
-            uint64_t jhi = __shfl_sync(0xffffffffu, (j < 32) ? c0hi : c1hi, owner);
-            const uint64_t ge_lo = (p < 64) ? (~0ull << p) : 0ull;
-            const uint64_t ge_hi = (p < 64) ? ~0ull : (~0ull << (p - 64));
-            const uint64_t clo = jlo & ge_lo, chi = jhi & ge_hi;
-            int t;
-            if (clo) t = __ffsll((long long)clo) - 1;
-            else if (chi) t = 64 + __ffsll((long long)chi) - 1;
-            else {
-                if (Wn < rows) { fail = true; break; }   // the pivot may lie outside the window
-                continue;                                // column j has no pivot
-            }
-            // exchange rows p and t in every 128-row mask
-            const uint64_t mp_lo = (p < 64) ? (1ull << p) : 0ull, mp_hi = (p < 64) ? 0ull : (1ull << (p - 64));
-            const uint64_t mt_lo = (t < 64) ? (1ull << t) : 0ull, mt_hi = (t < 64) ? 0ull : (1ull << (t - 64));
-            const uint64_t both_lo = mp_lo | mt_lo, both_hi = mp_hi | mt_hi;
-#define GF2_SWAPROWS(lo, hi)                                                        \
-            do {                                                                    \
-                const bool d_ = (((lo) & mp_lo) | ((hi) & mp_hi)) != 0ull;          \
-                const bool e_ = (((lo) & mt_lo) | ((hi) & mt_hi)) != 0ull;          \
-                if (d_ != e_) { (lo) ^= both_lo; (hi) ^= both_hi; }                 \
-            } while (0)
-            GF2_SWAPROWS(jlo, jhi);
-            const uint64_t gt_lo = (p >= 63) ? 0ull : (~0ull << (p + 1));
-            const uint64_t gt_hi = (p < 63) ? ~0ull : ((p - 63) >= 64 ? 0ull : (~0ull << (p - 63)));
-            const uint64_t rlo = jlo & gt_lo, rhi = jhi & gt_hi;   // rows below p holding column j
-            GF2_SWAPROWS(c0lo, c0hi);
-            GF2_SWAPROWS(c1lo, c1hi);
-            GF2_SWAPROWS(l0lo, l0hi);
-            GF2_SWAPROWS(l1lo, l1hi);
-#undef GF2_SWAPROWS
-            // the pivot row's entry in each owned column decides whether it is added
-            if (((c0lo & mp_lo) | (c0hi & mp_hi)) != 0ull) { c0lo ^= rlo; c0hi ^= rhi; }
-            if (((c1lo & mp_lo) | (c1hi & mp_hi)) != 0ull) { c1lo ^= rlo; c1hi ^= rhi; }
-            if (lane == (p & 31)) {
-                if (p < 32) { l0lo = rlo; l0hi = rhi; } else { l1lo = rlo; l1hi = rhi; }
-            }
-            if (lane == 0) {
-                sh.t[p] = t;
-                sh.j[p] = (uint8_t)j;
-                const int a = sh.perm[p];
-                sh.perm[p] = sh.perm[t];
-                sh.perm[t] = a;
-            }
-            tmax = max(tmax, t);
-            ++p;
+        // eliminate column j from the slots after t that hold it (slot t now
+        // holds the old row p, zero in column j)
+        const uint64_t elo = lo & ((t >= 63) ? 0ull : (~0ull << (t + 1)));
+        const uint64_t ehi = hi & ((t < 63) ? ~0ull : ((t - 63) >= 64 ? 0ull : (~0ull << (t - 63))));
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint64_t e = (b < 2) ? elo : ehi;
+            const uint64_t sel = 0ull - ((e >> ((32 * b + lane) & 63)) & 1ull);
+            R[b] ^= prow & sel;
+            Lc[b] |= (1ull << p) & sel;
         }
-        if (!fail) {
-            // rows 0..p-1 of the window now hold the pivots: transpose the column
-            // masks back into rows (lane r gets rows r and r + 32)
-            {
-                const unsigned e00 = transpose32((unsigned)c0lo), e01 = transpose32((unsigned)c1lo);
-                const unsigned e10 = transpose32((unsigned)(c0lo >> 32)), e11 = transpose32((unsigned)(c1lo >> 32));
-                const unsigned f00 = transpose32((unsigned)l0lo), f01 = transpose32((unsigned)l1lo);
-                const unsigned f10 = transpose32((unsigned)(l0lo >> 32)), f11 = transpose32((unsigned)(l1lo >> 32));
-                const int q0 = lane, q1 = lane + 32;
-                if (q0 < p) {
-                    sh.E[q0] = ((uint64_t)e01 << 32) | e00;
-                    sh.L[q0] = ((((uint64_t)f01 << 32) | f00)) & ((q0 == 0) ? 0ull : (~0ull >> (64 - q0)));
-                }
-                if (q1 < p) {
-                    sh.E[q1] = ((uint64_t)e11 << 32) | e10;
-                    sh.L[q1] = ((((uint64_t)f11 << 32) | f10)) & (~0ull >> (64 - q1));
-                }
-            }
-            __syncwarp();
-            // staged rows: pivot rows first, then rows displaced into [p, tmax]
-            for (int k = lane; k < p; k += 32) { sh.Soff[k] = k; sh.Ssrc[k] = r + sh.perm[k]; }
-            int base = p;
-            for (int b0 = p; b0 <= tmax; b0 += 32) {
-                const int sl = b0 + lane;
-                const bool mv = sl <= tmax && sh.perm[sl] != sl;
-                const unsigned bm = __ballot_sync(0xffffffffu, mv);
-                if (mv) {
-                    const int k = base + __popc(bm & ((1u << lane) - 1u));
-                    sh.Soff[k] = sl;
-                    sh.Ssrc[k] = r + sh.perm[sl];
-                }
-                base += __popc(bm);
-            }
-            if (lane == 0) { sh.nS = base; sh.maxpos = max(p - 1, tmax); }
+        if (lane == 0) {
+            sh.t[p] = t;
+            sh.j[p] = (uint8_t)j;
         }
-        if (lane == 0) { sh.fail = fail ? 1 : 0; sh.rbar = p; }
+        tmax = max(tmax, t);
+        ++p;
     }
+    if (!fail) {
+        // slots 0 .. p-1 hold the pivot rows (echelon); their L bits are below their index
+        if (lane < p) {
+            sh.E[lane] = R[0];
+            sh.L[lane] = Lc[0] & ((lane == 0) ? 0ull : (~0ull >> (64 - lane)));
+        }
+        if (lane + 32 < p) {
+            sh.E[lane + 32] = R[1];
+            sh.L[lane + 32] = Lc[1] & (~0ull >> (32 - lane));
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) sh.perm[32 * b + lane] = org[b];
+        __syncwarp();
+        // staged rows: pivot rows first, then rows displaced into [p, tmax]
+        for (int k = lane; k < p; k += 32) { sh.Soff[k] = k; sh.Ssrc[k] = r + sh.perm[k]; }
+        int base = p;
+        for (int b0 = p; b0 <= tmax; b0 += 32) {
+            const int sl = b0 + lane;
+            const bool mv = sl <= tmax && sh.perm[sl] != sl;
+            const unsigned bm = __ballot_sync(FULL, mv);
+            if (mv) {
+                const int k = base + __popc(bm & ((1u << lane) - 1u));
+                sh.Soff[k] = sl;
+                sh.Ssrc[k] = r + sh.perm[sl];
+            }
+            base += __popc(bm);
+        }
+        if (lane == 0) { sh.nS = base; sh.maxpos = max(p - 1, tmax); }
+    }
+    if (lane == 0) { sh.fail = fail ? 1 : 0; sh.rbar = p; }
+}
 
 // Block-wide path (every thread of the block): Algorithm 1's search over all
 // remaining rows.  Rows whose stripe word is zero can never hold a pivot and
@@ -324,8 +297,9 @@ __device__ __forceinline__ void panel_block(const uint64_t *__restrict__ A, int6
 
 // Rows of L11^-1 (L11 unit lower triangular, rows Lrows[0..rbar)), by one
 // warp: forward substitution per column (lane owns columns lane and
-// lane + 32), rows collected by ballot; lane 0 writes out[p].
-__device__ __forceinline__ void warp_lower_inverse(const uint64_t *Lrows, int rbar, uint64_t *out)
+// lane + 32), rows collected by ballot; lane 0 writes out[p] (and out2[p]).
+__device__ __forceinline__ void warp_lower_inverse(const uint64_t *Lrows, int rbar, uint64_t *out,
+                                                   uint64_t *out2 = nullptr)
 {
     const int lane = threadIdx.x & 31;
     uint64_t x0 = 0, x1 = 0;
@@ -337,7 +311,11 @@ __device__ __forceinline__ void warp_lower_inverse(const uint64_t *Lrows, int rb
     for (int p = 0; p < rbar; ++p) {
         const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
         const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
-        if (lane == 0) out[p] = ((uint64_t)hi << 32) | lo;
+        if (lane == 0) {
+            const uint64_t v = ((uint64_t)hi << 32) | lo;
+            out[p] = v;
+            if (out2) out2[p] = v;
+        }
     }
 }
 

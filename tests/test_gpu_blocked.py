@@ -14,10 +14,11 @@ from tests.test_gpu_parity import assert_ple_equal, make, ref_ple
 pytestmark = pytest.mark.gpu
 
 
-def handle(block, gemm_min_k=None, fmt=8):
+def handle(block, gemm_min_k=None, fmt=8, rref_block=None):
     import paper_1111_6549_gb300 as g
     h = g.Handle()
     h.set_option(g.OPT_PLE_BLOCK, block)
+    h.set_option(g.OPT_RREF_BLOCK, block if rref_block is None else rref_block)
     h.set_option(g.OPT_MUL_GEMM_FORMAT, fmt)
     if gemm_min_k is not None:
         h.set_option(g.OPT_MUL_GEMM_MIN_K, gemm_min_k)
@@ -71,11 +72,13 @@ def test_blocked_rref_and_solve():
         assert np.array_equal(to_host(dB, gi.words_for(nrhs)), B0)
 
 
+@pytest.mark.parametrize("rref_block", [128, 64])
 @pytest.mark.parametrize("m,n", [(700, 1500), (1500, 700), (640, 640)])
-def test_blocked_rref_wide_tall_and_exhausted(m, n):
+def test_blocked_rref_wide_tall_and_exhausted(m, n, rref_block):
     """Rank reaching m before the last block (wide), tall, and square: the RREF
-    built on the blocked PLE's stripe records."""
-    h = handle(128, 1)
+    built on the blocked PLE's stripe records, recursive down to one or two
+    stripes per block."""
+    h = handle(128, 1, rref_block=rref_block)
     A = make("dense", m, n, seed=m + 3 * n)
     dR = to_dev(A)
     Q = vec_dev(min(m, n))
@@ -86,8 +89,9 @@ def test_blocked_rref_wide_tall_and_exhausted(m, n):
     assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
 
 
+@pytest.mark.parametrize("rref_block", [640, 128])
 @pytest.mark.parametrize("dups", [(), (700,), (640,), (767, 768), (900, 1000, 1270, 1279), (1279,)])
-def test_blocked_rref_pivot_gaps(dups):
+def test_blocked_rref_pivot_gaps(dups, rref_block):
     """The right half's pivot columns with gaps (a column equal to an earlier
     one is no pivot): the gathered bits then come from scattered columns, and
     the left stripes skip only the words before the first gap."""
@@ -97,7 +101,7 @@ def test_blocked_rref_pivot_gaps(dups):
     for c in dups:
         U[:, c] = U[:, c - 37]
     A = gi.pack(U, A.shape[1])
-    h = handle(640, 1, 4 if len(dups) % 2 else 8)
+    h = handle(640, 1, 4 if len(dups) % 2 else 8, rref_block)
     dR = to_dev(A)
     Q = vec_dev(n)
     r = h.rref(dR, m, n, Q)
