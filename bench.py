@@ -472,6 +472,8 @@ def run_ours(args):
     h = g.Handle(local)
     if args.tma:
         h.set_option(g.OPT_TMA_UPDATE, 1)
+    if args.paired:
+        h.set_option(g.OPT_WIDE_UPDATE, 0)
     if args.ple_block is not None:
         h.set_option(g.OPT_PLE_BLOCK, args.ple_block)
     if args.gemm_format is not None:
@@ -727,6 +729,8 @@ def main():
                     help="base block width of the recursive RREF recovery (0: flat; default: the library's)")
     ap.add_argument("--ple-block", type=int, default=None,
                     help="PLE column block for the blocked trailing update (GF2_OPT_PLE_BLOCK)")
+    ap.add_argument("--paired", action="store_true",
+                    help="table updates in the paired 64-byte-tile form (GF2_OPT_WIDE_UPDATE = 0)")
     ap.add_argument("--tma", action="store_true",
                     help="run the update in its TMA-staged form (GF2_OPT_TMA_UPDATE)")
     ap.add_argument("--tc-compare", action="store_true",

@@ -335,6 +335,11 @@ int gf2_server_destroy(gf2_server_t server);
  *                      table pass per stripe over all rows above it; -1
  *                      (default): blocks of 16384 columns from 65536 pivot
  *                      columns on, else 0
+ *   GF2_OPT_WIDE_UPDATE the table updates on 16-byte aligned rows take
+ *                      128-byte column tiles with nine tables per stripe
+ *                      (eight of 7 bits, one of 8 bits; default on); 0: two
+ *                      CTAs share each 128-byte line, 64 bytes each, with
+ *                      eight 8-bit tables
  * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
@@ -349,6 +354,7 @@ int gf2_server_destroy(gf2_server_t server);
 #define GF2_OPT_PLE_BLOCK       6
 #define GF2_OPT_MUL_GEMM_FORMAT 7
 #define GF2_OPT_RREF_BLOCK      8
+#define GF2_OPT_WIDE_UPDATE     9
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */

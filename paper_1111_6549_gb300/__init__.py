@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
 (OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE, OPT_TMA_UPDATE, OPT_MUL_GEMM_MIN_K, OPT_PLE_BLOCK,
- OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK) = 1, 2, 3, 4, 5, 6, 7, 8
+ OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE) = 1, 2, 3, 4, 5, 6, 7, 8, 9
 BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
 
@@ -332,7 +332,8 @@ class Handle:
         return int(load().gf2_selftest_wait(self._h, int(limit_us)))
 
     def set_option(self, option: int, value: int) -> None:
-        """OPT_LOOKAHEAD / OPT_TC_MUL / OPT_TC_UPDATE / OPT_TMA_UPDATE (0 off, 1 on); results are identical."""
+        """An OPT_* execution option (gf2_set_option): switches take 0 / 1, block widths a
+        multiple of 64 (0 off, -1 automatic), OPT_MUL_GEMM_FORMAT 4 or 8; results are identical."""
         _check(load().gf2_set_option(self._h, option, int(value)), "gf2_set_option")
 
     # ---- statistics -----------------------------------------------------

@@ -49,6 +49,7 @@ struct gf2_handle {
     int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the library GEMM
     int gemm_fmt = 4;              // its operand format: 4 = FP4 E2M1 (block scales 1), 8 = FP8 E4M3
     int64_t rref_block = -1;       // RREF recovery: base block width of the recursive form (0: flat, -1: auto)
+    bool wide_update = true;       // table updates on aligned rows: 128-byte tiles, nine tables
     int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
     char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
     size_t lbuf_cap = 0;
@@ -201,6 +202,7 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
     if (!timed) a.bytes = nullptr;
     else if (h->profiling) h->upd_timed += 1;
     a.err = err_dev(h);
+    a.wide = h->wide_update ? 1 : 0;
     const bool tc = (a.mode == UPD_MUL) ? h->tc_mul : (a.mode == UPD_M4RI ? false : h->tc_update);
     a.tmap = nullptr;
     if (!tc && h->tma && a.mode != UPD_M4RI) {
@@ -1440,6 +1442,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
         if (value < -1 || (value > 0 && value % 64)) return GF2_EINVAL;
         h->rref_block = value;
         return GF2_OK;
+    case GF2_OPT_WIDE_UPDATE: h->wide_update = value != 0; return GF2_OK;
     case GF2_OPT_MUL_GEMM_FORMAT:
         if (value != 8 && value != 4) return GF2_EINVAL;
         h->gemm_fmt = (int)value;

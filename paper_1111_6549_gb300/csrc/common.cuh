@@ -17,6 +17,11 @@ constexpr int TW = 8;             // update tile width in words (64 bytes per ro
 constexpr int NTAB = KS / 8;      // 8-bit tables per stripe
 constexpr int TAB_LINE = 2 * TW;  // words per shared-memory line (two tables interleaved)
 constexpr int TAB_WORDS = (NTAB / 2) * 256 * TAB_LINE;  // 16384 words = 128 KiB
+// Wide form of the update: 128-byte tiles, eight 7-bit tables + one 8-bit
+// table per stripe (entry e of table t at entry offset 128 t + e).
+constexpr int WT = 16;            // wide tile width in words (128 bytes per row)
+constexpr int WNTAB = 9;
+constexpr int WIDE_TAB_WORDS = (8 * 128 + 256) * WT;    // 20480 words = 160 KiB
 constexpr int UPD_THREADS = 512;
 constexpr int UPD_ROWS_PER_THREAD = 4;
 constexpr int PANEL_THREADS = 512;
@@ -106,6 +111,7 @@ struct UpdArgs {
     int32_t *err;              // device error word (bounded waits that expire), may be null
     const struct TensorMap2D *tmap;  // TMA descriptor of A's rows (null: plain loads and stores)
     int64_t W_full;            // PLE: row width; staged rows also get words [W, W_full) (0: none)
+    int wide;                  // aligned rows: 128-byte tiles with nine tables (else paired 64-byte tiles)
 };
 
 // A CUtensorMap (128 bytes) kept opaque outside the files that use TMA.

@@ -209,6 +209,18 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
 //    lookups per word already use heavily.  Loads and stores use the default
 //    cache policy: evict-first hints let L2 drop the partner half of a line
 //    before the paired CTA reads it (measured: reads back up to 1.68x).
+//
+// WIDE = true: 128-byte column tiles, so that every warp-wide row load or
+// store covers whole 128-byte lines (four rows of eight lanes) instead of
+// half lines (eight rows of four lanes): half the L1 wavefronts per byte of
+// row, which with the table lookups saturate the L1/shared data pipe.  Eight
+// 8-bit tables of 128-byte entries would take 256 KiB, so a stripe's 64
+// generator rows are split into eight 7-bit tables (rows 7t .. 7t+6, 128
+// entries) and one 8-bit table (rows 56..63): 1280 entries x 128 bytes =
+// 160 KiB, nine lookups per 16 bytes of row instead of eight.  Index bit j
+// still selects generator row j.  The eight lanes of a row read one whole
+// 128-byte entry per lookup, so lookups are conflict-free; CTAs take whole
+// lines and need no partner.
 constexpr int PIPE_RPT = 4;
 
 struct RowBatch {
@@ -216,6 +228,7 @@ struct RowBatch {
     int64_t ri[PIPE_RPT];
 };
 
+template <bool WIDE>
 __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
 {
     extern __shared__ __align__(16) uint64_t T[];
@@ -281,29 +294,34 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
 
     const int64_t R = row_hi - row_lo;
     if (R <= 0 || w_lo >= W) return;
-    const int64_t a0 = w_lo / TW, a1 = (W + TW - 1) / TW;
+    // The column range in units: tile pairs of 64-byte tiles (paired form),
+    // 128-byte tiles (wide form); tp_lo / tp_hi select a range of units, and
+    // unit 0 holds the first word w_lo either way.
+    constexpr int TWK = WIDE ? WT : TW;              // words per tile
+    const int64_t a0 = w_lo / TWK, a1 = (W + TWK - 1) / TWK;
     const int64_t NT = a1 - a0;
-    const int64_t NTP = (NT + 1) / 2;
-    const int64_t tp_lo = min(a.tp_lo, NTP);
-    const int64_t tp_hi = (a.tp_hi < 0) ? NTP : min(a.tp_hi, NTP);
+    const int64_t NU = WIDE ? NT : (NT + 1) / 2;
+    const int64_t tp_lo = min(a.tp_lo, NU);
+    const int64_t tp_hi = (a.tp_hi < 0) ? NU : min(a.tp_hi, NU);
     if (tp_lo >= tp_hi) return;
-    const int npairs = gridDim.x >> 1;
-    const int pj = blockIdx.x >> 1, half = blockIdx.x & 1;
+    const int npairs = WIDE ? (int)gridDim.x : (int)(gridDim.x >> 1);
+    const int pj = WIDE ? (int)blockIdx.x : (int)(blockIdx.x >> 1), half = WIDE ? 0 : (int)(blockIdx.x & 1);
     if (pj >= npairs) return;                       // odd grid: the last CTA has no partner
     const int64_t U = (tp_hi - tp_lo) * R;
     const int64_t u_beg = U * pj / npairs;
     const int64_t u_end = U * (pj + 1) / npairs;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.bytes) {
-        const int64_t wl = max(w_lo, (a0 + 2 * tp_lo) * TW);
-        const int64_t wh = min(W, (a0 + 2 * tp_hi) * TW);
+        const int64_t wl = max(w_lo, (a0 + (WIDE ? 1 : 2) * tp_lo) * TWK);
+        const int64_t wh = min(W, (a0 + (WIDE ? 1 : 2) * tp_hi) * TWK);
         atomicAdd(a.bytes, (unsigned long long)(R * (wh - wl) * 16));
     }
 
+    constexpr int LANES = TWK / 2;                  // threads per row: 16 bytes each
     const int tid = threadIdx.x;
-    const int rs = tid >> 2;
-    const int qd = tid & 3;
+    const int rs = tid / LANES;
+    const int qd = tid % LANES;
     const int rho = rs & 1;
-    constexpr int SLOTS = UPD_THREADS / 4;
+    constexpr int SLOTS = UPD_THREADS / LANES;
     constexpr int CH = SLOTS * PIPE_RPT;             // rows per batch
 
     for (int64_t u = u_beg; u < u_end;) {
@@ -311,11 +329,12 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
         const int64_t rr0 = u - tq * R;
         const int64_t nrows = min(R - rr0, u_end - u);
         u += nrows;
-        const int64_t tile = 2 * (tp_lo + tq) + half;
+        const int64_t tile = WIDE ? tp_lo + tq : 2 * (tp_lo + tq) + half;
         if (tile >= NT) continue;
-        const int64_t wbase = (a0 + tile) * TW;
+        const int64_t wbase = (a0 + tile) * TWK;
         __syncthreads();
-        build_tables(T, sGen, wbase, W);
+        if (WIDE) build_wide_tables(T, sGen, wbase, W);
+        else build_tables(T, sGen, wbase, W);
         __syncthreads();
 
         const int64_t w0 = wbase + 2 * qd;
@@ -358,14 +377,25 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
             for (int k = 0; k < PIPE_RPT; ++k) {
                 uint64_t x0 = bt.x0[k], x1 = bt.x1[k];
                 const uint64_t ix = bt.ix[k];
+                if (WIDE) {
 #pragma unroll
-                for (int uu = 0; uu < NTAB; ++uu) {
-                    const int tau = uu ^ rho;
-                    const int e = (int)((ix >> (8 * tau)) & 255ull);
-                    const ulonglong2 tv = *reinterpret_cast<const ulonglong2 *>(
-                        Tq + (tau >> 1) * (256 * TAB_LINE) + e * TAB_LINE + (tau & 1) * TW);
-                    x0 ^= tv.x;
-                    x1 ^= tv.y;
+                    for (int t = 0; t < WNTAB; ++t) {
+                        const int e = t < WNTAB - 1 ? (int)((ix >> (7 * t)) & 127ull) : (int)(ix >> 56);
+                        const ulonglong2 tv =
+                            *reinterpret_cast<const ulonglong2 *>(Tq + (int64_t)(128 * t + e) * WT);
+                        x0 ^= tv.x;
+                        x1 ^= tv.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int uu = 0; uu < NTAB; ++uu) {
+                        const int tau = uu ^ rho;
+                        const int e = (int)((ix >> (8 * tau)) & 255ull);
+                        const ulonglong2 tv = *reinterpret_cast<const ulonglong2 *>(
+                            Tq + (tau >> 1) * (256 * TAB_LINE) + e * TAB_LINE + (tau & 1) * TW);
+                        x0 ^= tv.x;
+                        x1 ^= tv.y;
+                    }
                 }
                 if (bt.ri[k] < 0) continue;
                 uint64_t *dst = a.A + bt.ri[k] * a.ld;
@@ -402,7 +432,10 @@ cudaError_t setup_update_kernel()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(update_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(update_pipe_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(update_pipe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(WIDE_TAB_WORDS * sizeof(uint64_t)));
     if (e != cudaSuccess) return e;
     e = setup_update_tma_kernel();
     if (e != cudaSuccess) return e;
@@ -429,7 +462,12 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
         if (grid < 2) grid = 2;
         if (a.tmap)
             return launch_update_tma(st, a, grid);
-        update_pipe_kernel<<<grid, UPD_THREADS, smem, st>>>(a);
+        if (a.wide) {
+            int gw = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
+            update_pipe_kernel<true><<<gw, UPD_THREADS, WIDE_TAB_WORDS * sizeof(uint64_t), st>>>(a);
+        } else {
+            update_pipe_kernel<false><<<grid, UPD_THREADS, smem, st>>>(a);
+        }
     } else {
         update_kernel<false><<<grid, UPD_THREADS, smem, st>>>(a);
     }

@@ -40,4 +40,39 @@ __device__ __forceinline__ void build_tables(uint64_t *T, const uint64_t *const 
     }
 }
 
+// Wide form: 128-byte tiles (WT words), table t < 8 holding the 128
+// combinations of generator rows 7t .. 7t+6, table 8 the 256 combinations of
+// rows 56 .. 63.  Work items are (32-entry segment, word): 8 x 4 + 8 = 40
+// segments x 16 words = 640 items over the block's threads; each item walks
+// its segment in Gray-code order (31 additions after the segment's base).
+__device__ __forceinline__ void build_wide_tables(uint64_t *T, const uint64_t *const *gen, int64_t wbase,
+                                                  int64_t W)
+{
+    for (int item = threadIdx.x; item < 40 * WT; item += blockDim.x) {
+        const int w = item % WT, seg = item / WT;
+        const int t = seg < 32 ? seg >> 2 : 8;       // table
+        const int q = seg < 32 ? seg & 3 : seg - 32; // segment: index bits 5.. of the table
+        const int nb = t < 8 ? 7 : 8;                // index bits of the table
+        const int64_t word = wbase + w;
+        const bool inr = word < W;
+        uint64_t g[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint64_t *p = b < nb ? gen[7 * t + b] : nullptr;
+            g[b] = (p != nullptr && inr) ? p[word] : 0ull;
+        }
+        uint64_t val = ((q & 1) ? g[5] : 0ull) ^ ((q & 2) ? g[6] : 0ull) ^ ((q & 4) ? g[7] : 0ull);
+        uint64_t *Tt = T + (int64_t)(128 * t + 32 * q) * WT + w;
+        int x = 0;
+        Tt[0] = val;
+#pragma unroll
+        for (int i = 1; i < 32; ++i) {
+            const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4;
+            x ^= 1 << b;
+            val ^= g[b];
+            Tt[x * WT] = val;
+        }
+    }
+}
+
 }  // namespace gf2

@@ -1,5 +1,7 @@
-"""The tensor-core (tcgen05) forms of the product and of the trailing
-updates: bit-exact against the oracle, like the table forms."""
+"""The alternative forms of the product and of the trailing updates -- the
+tensor-core (tcgen05) kernels, the library GEMM, the TMA-staged and the
+paired 64-byte-tile table updates: bit-exact against the oracle, like the
+default forms."""
 import numpy as np
 import pytest
 
@@ -78,6 +80,40 @@ def test_tma_update_ple_rref_and_mul(m, n):
     R0 = A.copy()
     oracle.rref(R0, m, n)
     assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+    k = 200
+    B = gi.bernoulli_matrix(k, n, 3)
+    X = gi.bernoulli_matrix(m, k, 4)
+    C0 = gi.bernoulli_matrix(m, n, 5)
+    dC = to_dev(C0)
+    hh.mul(dC, to_dev(X), to_dev(B), m, k, n, accumulate=True)
+    want = C0.copy()
+    oracle.mul(X, B, m, k, n, C=want, accumulate=True)
+    assert np.array_equal(to_host(dC), want)
+
+
+@pytest.mark.parametrize("m,n", [(300, 1100), (1000, 1500), (2048, 2048), (4099, 1030), (2500, 3000)])
+def test_paired_update_ple_rref_m4ri_and_mul(m, n):
+    """The paired 64-byte-tile form of the table update (GF2_OPT_WIDE_UPDATE = 0;
+    the default runs 128-byte tiles with nine tables)."""
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    hh.set_option(g.OPT_WIDE_UPDATE, 0)
+    A = gi.bernoulli_matrix(m, n, 5 * m + n)
+    dA = to_dev(A)
+    P, Q = vec_dev(m), vec_dev(min(m, n))
+    r = hh.ple(dA, m, n, P, Q)
+    LE = A.copy()
+    r0, P0, Q0 = oracle.ple(LE, m, n)
+    assert r == r0 and np.array_equal(P.cpu().numpy()[:m], P0)
+    assert np.array_equal(to_host(dA, gi.words_for(n)), LE)
+    R0 = A.copy()
+    oracle.rref(R0, m, n)
+    dR = to_dev(A)
+    assert hh.rref(dR, m, n, Q) == r0
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+    dM = to_dev(A)
+    assert hh.rref_m4ri(dM, m, n, Q) == r0
+    assert np.array_equal(to_host(dM, gi.words_for(n)), R0)
     k = 200
     B = gi.bernoulli_matrix(k, n, 3)
     X = gi.bernoulli_matrix(m, k, 4)
