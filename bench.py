@@ -548,8 +548,9 @@ def run_ours(args):
                 "frac_of_nominal_8000": (upd_gbs / 8000.0) if upd_gbs else None,
                 "traffic": traffic, "algorithmic_bytes_per_launch": upd_per_launch_bytes,
                 "traffic_source": (f"{ratio_src}: ncu dram__bytes_read.sum + dram__bytes_write.sum over "
-                                   f"the update launches of a 32768^2 capture, {ratio:.3f} DRAM bytes per "
-                                   f"algorithmic byte, scaled to this launch size") if ratio else None,
+                                   f"every update launch of one captured 65536^2 step, {ratio:.4f} DRAM bytes "
+                                   f"per algorithmic byte, times this run's algorithmic bytes per launch")
+                                  if ratio else None,
                 "launches_per_step": st["update_launches"] / args.steps,
                 "timed_launches": st["update_timed_launches"],
                 "update_share_of_step_diagnostic": None,
