@@ -542,7 +542,8 @@ def run_ours(args):
     upd_per_launch_bytes = st["update_bytes"] / max(st["update_timed_launches"], 1)
     ratio, ratio_src = update_kernel_traffic()
     traffic = ratio * upd_per_launch_bytes if ratio is not None else None
-    roofline = {"kernel": "update_kernel (tabulated trailing update, PLE + RREF passes)",
+    roofline = {"kernel": "update_pipe_kernel (tabulated trailing update: PLE stripes, TRSM and RREF passes; "
+                          + ("paired 64-byte tiles)" if args.paired else "wide 128-byte tiles)"),
                 "bound": "hbm", "achieved": upd_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (upd_gbs / hbm) if upd_gbs else None, "peak_kind": hbm_kind,
                 "frac_of_nominal_8000": (upd_gbs / 8000.0) if upd_gbs else None,
