@@ -59,3 +59,20 @@ def test_library_built_for_sm103a():
     from paper_1111_6549_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
     assert os.path.exists(build.LIB)
+
+
+def test_binding_constants_match_the_header():
+    """Every status, solve-status and option number the Python binding uses is
+    the one include/gf2.h defines (the binding marshals plain integers)."""
+    import paper_1111_6549_gb300 as g
+    defines = dict((k, int(v)) for k, v in
+                   re.findall(r"^#define\s+(GF2_[A-Z0-9_]+)\s+(-?\d+)", open(HEADER).read(), flags=re.M))
+    checked = 0
+    for name, value in defines.items():
+        py = name if name.startswith(("GF2_OK", "GF2_E")) else name[len("GF2_"):]
+        if hasattr(g, py):
+            assert getattr(g, py) == value, (name, getattr(g, py), value)
+            checked += 1
+    opts = [k for k in defines if k.startswith("GF2_OPT_")]
+    assert opts and all(hasattr(g, k[len("GF2_"):]) for k in opts)
+    assert checked >= len(opts) + 6 + 3
