@@ -235,7 +235,9 @@ int gf2_rref_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_
  * that must not stall on cudaMalloc / cudaFree -- and it needs no handle
  * (creating one allocates).
  *   A, P, Q, rank  as gf2_ple (A, P, Q device pointers; rank a host int64*).
- *   stream         a cudaStream_t passed as void* (NULL: the default stream).
+ *   stream         a cudaStream_t passed as void* (NULL: the default stream);
+ *                  it must belong to the current device (GF2_EINVAL if not),
+ *                  since the scratch address used is the current device's.
  * Limits: m <= 4096 and n <= 4096; larger sizes return GF2_EINVAL and enqueue
  * nothing.  Scratch: one fixed array of about 0.5 MiB inside the library,
  * held on every GPU that loads the library until the process exits.  The
@@ -340,6 +342,10 @@ int gf2_server_destroy(gf2_server_t server);
  *                      (eight of 7 bits, one of 8 bits; default on); 0: two
  *                      CTAs share each 128-byte line, 64 bytes each, with
  *                      eight 8-bit tables
+ *   GF2_OPT_NAIVE_UPDATE the plain baseline (default off): every trailing
+ *                      update (PLE stripes, RREF passes, table products) adds
+ *                      the selected generator rows one by one, with no
+ *                      tables; for measuring what the tables buy
  * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
@@ -355,6 +361,7 @@ int gf2_server_destroy(gf2_server_t server);
 #define GF2_OPT_MUL_GEMM_FORMAT 7
 #define GF2_OPT_RREF_BLOCK      8
 #define GF2_OPT_WIDE_UPDATE     9
+#define GF2_OPT_NAIVE_UPDATE    10
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */
@@ -379,6 +386,41 @@ int gf2_set_profiling(gf2_handle_t handle, int on);
 /* Read the counters (synchronises the stream to finish the event timing). */
 int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);
 int gf2_reset_stats(gf2_handle_t handle);
+
+/*
+ * Tensor-core carriers of a GF(2) product (Section 3.3: the block step of
+ * Algorithm 3 is a matrix multiplication; over GF(2) it is an integer
+ * product of 0/1 matrices reduced mod 2).  Three carriers run on sm_103a:
+ *   GF2_CARRIER_B1   warp-level mma.sync m16n8k256 on 1-bit operands, AND and
+ *                    population count into int32 counts;
+ *   GF2_CARRIER_FP8  tcgen05.mma kind::f8f6f4 on E4M3 0/1 (M128 N256 K32);
+ *   GF2_CARRIER_FP4  tcgen05.mma kind::mxf4 block-scaled, E2M1 0/1 packed two
+ *                    per byte, scales 2^0 (M128 N256 K64).
+ * (The integer tensor-core form kind::i8 is not accepted for sm_103a.)
+ * Both calls use the current device and its default stream, allocate a few
+ * bytes of device memory and synchronise the device.
+ *
+ * gf2_carrier_check: one product of bit matrices given as DEVICE words.
+ *   B1:       a_bits 16 rows x 4 words (256 bits), b_bits 8 columns x 4
+ *             words; counts int32[16 x 8], counts[i * 8 + j] = popcount of
+ *             (row i AND column j).
+ *   FP8, FP4: a_bits 128 rows x 1 word, b_bits 256 columns x 1 word; counts
+ *             int32[128 x 256], counts[i * 256 + j] = popcount(a[i] & b[j]).
+ * gf2_carrier_rate: `iters` instruction steps per warp (B1: four independent
+ *   m16n8k256 per step, 8 warps per CTA, 4 CTAs per SM) or per CTA (FP8: two
+ *   K32 MMAs, FP4: one K64 MMA per step, one CTA per SM) on all-ones
+ *   operands held in registers or shared memory; *macs_per_s = multiply-adds
+ *   per second over the whole GPU, *count_out (may be NULL) = one final
+ *   count (iters * 256 for B1, iters * 64 otherwise).  GF2_EINVAL when a
+ *   count would not stay exact (iters * 256 >= 2^31 for B1, iters * 64 >=
+ *   2^24 otherwise); GF2_ETIMEOUT when a bounded wait for the tensor cores
+ *   ran out.
+ */
+#define GF2_CARRIER_B1  1
+#define GF2_CARRIER_FP4 4
+#define GF2_CARRIER_FP8 8
+int gf2_carrier_check(int carrier, const uint64_t *a_bits, const uint64_t *b_bits, int32_t *counts);
+int gf2_carrier_rate(int carrier, int64_t iters, double *macs_per_s, int64_t *count_out);
 
 /*
  * Failure-detection self-test (no counterpart in the paper): runs one kernel

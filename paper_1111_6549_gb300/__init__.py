@@ -25,9 +25,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
 (OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE, OPT_TMA_UPDATE, OPT_MUL_GEMM_MIN_K, OPT_PLE_BLOCK,
- OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE) = 1, 2, 3, 4, 5, 6, 7, 8, 9
+ OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE, OPT_NAIVE_UPDATE) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
 BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
+CARRIER_B1, CARRIER_FP4, CARRIER_FP8 = 1, 4, 8
 
 
 class GF2Error(RuntimeError):
@@ -121,6 +122,8 @@ def load():
             "gf2_server_drain": ([vp], ctypes.c_int),
             "gf2_server_clock": ([], ctypes.c_double),
             "gf2_server_destroy": ([vp], ctypes.c_int),
+            "gf2_carrier_check": ([ctypes.c_int, vp, vp, vp], ctypes.c_int),
+            "gf2_carrier_rate": ([ctypes.c_int, i64, ctypes.POINTER(ctypes.c_double), i64p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -407,6 +410,21 @@ def ple_noalloc(A, m: int, n: int, P, Q) -> int:
     _check(f(_dptr(A), m, n, ld, _dptr(P), _dptr(Q), ctypes.byref(rank), ctypes.c_void_p(s)),
            "gf2_ple_noalloc")
     return rank.value
+
+
+def carrier_check(carrier: int, a_bits, b_bits, counts) -> None:
+    """gf2_carrier_check: one product of bit matrices (device int64 tensors)
+    on the given tensor-core carrier; counts (device int32) receives the
+    AND-population counts."""
+    _check(load().gf2_carrier_check(carrier, _dptr(a_bits), _dptr(b_bits), _dptr(counts)), "gf2_carrier_check")
+
+
+def carrier_rate(carrier: int, iters: int):
+    """gf2_carrier_rate: (multiply-adds per second over the GPU, final count)."""
+    rate = ctypes.c_double(0.0)
+    cnt = ctypes.c_int64(0)
+    _check(load().gf2_carrier_rate(carrier, iters, ctypes.byref(rate), ctypes.byref(cnt)), "gf2_carrier_rate")
+    return rate.value, cnt.value
 
 
 class Server:

@@ -50,6 +50,7 @@ struct gf2_handle {
     int gemm_fmt = 4;              // its operand format: 4 = FP4 E2M1 (block scales 1), 8 = FP8 E4M3
     int64_t rref_block = -1;       // RREF recovery: base block width of the recursive form (0: flat, -1: auto)
     bool wide_update = true;       // table updates on aligned rows: 128-byte tiles, nine tables
+    bool naive_update = false;     // plain baseline: trailing updates as one-by-one row additions
     int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
     char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
     size_t lbuf_cap = 0;
@@ -203,6 +204,7 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
     else if (h->profiling) h->upd_timed += 1;
     a.err = err_dev(h);
     a.wide = h->wide_update ? 1 : 0;
+    a.naive = h->naive_update ? 1 : 0;
     const bool tc = (a.mode == UPD_MUL) ? h->tc_mul : (a.mode == UPD_M4RI ? false : h->tc_update);
     a.tmap = nullptr;
     if (!tc && h->tma && a.mode != UPD_M4RI) {
@@ -301,7 +303,7 @@ int run_ple_range(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
     probe.ld = ld;
     probe.S = S;
     probe.ldS = L.ldS;
-    const bool la = h->lookahead && !h->tc_update && h->side && s_hi - s_lo > 1 && update_vectorised(probe) &&
+    const bool la = h->lookahead && !h->tc_update && !h->naive_update && h->side && s_hi - s_lo > 1 && update_vectorised(probe) &&
                     h->num_sms >= 8;
     if (!la) {
         for (int64_t s = s_lo; s < s_hi; ++s) {
@@ -921,6 +923,55 @@ static int mul_gemm(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, 
     return GF2_OK;
 }
 
+// C ^= A B through the own FP4 tcgen05 GEMM (kernels_gemm_f4.cu): per chunk
+// of at most 2^22 inner bits (the fp32 counts stay exact and below 2^23), B
+// is expanded once to B^T in FP4 and A in row blocks of at most 2^15 rows;
+// the GEMM's epilogue XORs the parities into C, so no count reaches memory.
+// The expanded operands are padded to whole TMA boxes (256 rows of A, 192 of
+// B^T, 128 bytes of inner dimension) with zeros.
+static int mul_own(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
+                   int64_t ldb, int64_t m, int64_t k, int64_t n)
+{
+    constexpr int64_t KCH = int64_t(1) << 22;
+    constexpr int64_t MB = int64_t(1) << 15;
+    for (int64_t k0 = 0; k0 < k; k0 += KCH) {
+        const int64_t kc = std::min(KCH, k - k0);
+        const int64_t kp = (kc + 255) & ~int64_t(255);
+        const size_t rowb = (size_t)kp / 2;
+        const int64_t np = std::max<int64_t>(n, 192);
+        const int64_t mb = std::min(m, MB);
+        const int64_t mbp = std::max<int64_t>(mb, 256);
+        const size_t bbytes = align256((size_t)np * rowb), abytes = align256((size_t)mbp * rowb);
+        int rc = grow(&h->gbuf, &h->gbuf_cap, bbytes + abytes, h->stream);
+        if (rc) return rc;
+        uint8_t *B4t = reinterpret_cast<uint8_t *>(h->gbuf);
+        uint8_t *A4 = reinterpret_cast<uint8_t *>(h->gbuf + bbytes);
+        {
+            Timed t(h, K_OTHER);
+            CK(launch_expand_transpose(h->stream, 4, B + k0 * ldb, ldb, 0, kc, n, kp, B4t, h->num_sms));
+        }
+        h->launches += 1;
+        if (np > n) CK(cudaMemsetAsync(B4t + (size_t)n * rowb, 0, (size_t)(np - n) * rowb, h->stream));
+        for (int64_t i0 = 0; i0 < m; i0 += mb) {
+            const int64_t rows = std::min(mb, m - i0);
+            {
+                Timed t(h, K_OTHER);
+                CK(launch_expand_rows(h->stream, 4, A + i0 * lda, lda, rows, k0, k0 + kc, kp, A4, h->num_sms));
+            }
+            const int64_t rows_p = std::max<int64_t>(rows, 256);
+            if (rows_p > rows)
+                CK(cudaMemsetAsync(A4 + (size_t)rows * rowb, 0, (size_t)(rows_p - rows) * rowb, h->stream));
+            {
+                Timed t(h, K_OTHER);
+                CK(launch_gemm_f4(h->stream, C + i0 * ldc, ldc, A4, rows_p, B4t, np, rows, n, kp, err_dev(h),
+                                  h->num_sms));
+            }
+            h->launches += 2;
+        }
+    }
+    return GF2_OK;
+}
+
 int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
             int64_t ldb, int64_t m, int64_t k, int64_t n, int accumulate)
 {
@@ -932,7 +983,9 @@ int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t
     const int64_t Wc = words_for(n);
     if (!accumulate)
         CK(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)Wc * 8, (size_t)m, h->stream));
-    if (!h->tc_mul && h->gemm_min_k > 0 && k >= h->gemm_min_k) return mul_gemm(h, C, ldc, A, lda, B, ldb, m, k, n);
+    if (!h->tc_mul && h->gemm_min_k > 0 && k >= h->gemm_min_k)
+        return h->gemm_fmt == 0 ? mul_own(h, C, ldc, A, lda, B, ldb, m, k, n)
+                                : mul_gemm(h, C, ldc, A, lda, B, ldb, m, k, n);
     if (h->tc_mul && k > 0) {
         // tensor cores, pipelined tcgen05 kernel: the counts of every inner
         // chunk accumulate in tensor memory, so C is read and written once per
@@ -1443,8 +1496,9 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
         h->rref_block = value;
         return GF2_OK;
     case GF2_OPT_WIDE_UPDATE: h->wide_update = value != 0; return GF2_OK;
+    case GF2_OPT_NAIVE_UPDATE: h->naive_update = value != 0; return GF2_OK;
     case GF2_OPT_MUL_GEMM_FORMAT:
-        if (value != 8 && value != 4) return GF2_EINVAL;
+        if (value != 8 && value != 4 && value != 0) return GF2_EINVAL;
         h->gemm_fmt = (int)value;
         return GF2_OK;
     case GF2_OPT_MUL_GEMM_MIN_K:

@@ -112,6 +112,7 @@ struct UpdArgs {
     const struct TensorMap2D *tmap;  // TMA descriptor of A's rows (null: plain loads and stores)
     int64_t W_full;            // PLE: row width; staged rows also get words [W, W_full) (0: none)
     int wide;                  // aligned rows: 128-byte tiles with nine tables (else paired 64-byte tiles)
+    int naive;                 // plain baseline: generator rows added one by one, no tables
 };
 
 // A CUtensorMap (128 bytes) kept opaque outside the files that use TMA.
@@ -150,6 +151,14 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
+// GF(2) product through the own FP4 tcgen05 GEMM (kernels_gemm_f4.cu): A4
+// a_rows >= max(m, 256) and B4t b_rows >= max(n, 192) rows of kp / 2 bytes
+// each (expanded operands, zero past m / n rows; kp a multiple of 256);
+// C (m x n bits) ^= the parities of A4 B4t^T.
+cudaError_t launch_gemm_f4(cudaStream_t st, uint64_t *C, int64_t ldc, const uint8_t *A4, int64_t a_rows,
+                           const uint8_t *B4t, int64_t b_rows, int64_t m, int64_t n, int64_t kp, int32_t *err,
+                           int num_sms);
+bool encode_f4_operand(TensorMap2D *out, const uint8_t *base, int64_t rows, int64_t rowb, int box_rows);
 // GF(2) product through a library FP4 / FP8 GEMM (kernels_gemm.cu)
 cudaError_t launch_expand_rows(cudaStream_t st, int fmt, const uint64_t *A, int64_t lda, int64_t rows, int64_t k0,
                                int64_t k, int64_t kp, uint8_t *out, int num_sms);

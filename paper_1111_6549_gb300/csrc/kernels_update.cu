@@ -424,6 +424,77 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     }
 }
 
+
+// ----------------------------------------------------------------------------
+// Naive form, the plain baseline: no tables.  One thread per (row, word) adds
+// the generator rows selected by the row's index bits one by one (up to 64
+// row additions per row, Section 3.2's trailing update written as plain row
+// XORs), so every updated word reads up to 64 generator words.  Same modes
+// and arguments as the table kernels (PLE, RREF, MUL).
+__global__ void __launch_bounds__(256) naive_update_kernel(UpdArgs a)
+{
+    __shared__ const uint64_t *sGen[KS];
+    int64_t row_lo, row_hi, w_lo, r = 0;
+    int maxpos = -1, nS = 0;
+    const int64_t W = a.W;
+    const StripeDesc *d = a.desc;
+    if (a.mode == UPD_PLE) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        r = d->r;
+        row_lo = r;
+        row_hi = a.m;
+        w_lo = (d->c >> 6) + 1;
+        maxpos = d->maxpos;
+        nS = d->nS;
+        if (threadIdx.x < KS) sGen[threadIdx.x] = (threadIdx.x < rbar) ? a.S + threadIdx.x * a.ldS : nullptr;
+    } else if (a.mode == UPD_RREF) {
+        const int rbar = d->rbar;
+        if (rbar == 0) return;
+        row_lo = a.row_lo;
+        row_hi = d->r;
+        w_lo = max((int64_t)(d->c >> 6), a.w_lo);
+        if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
+        __syncthreads();
+        if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;
+    } else {
+        row_lo = a.row_lo;
+        row_hi = a.row_hi;
+        w_lo = a.w_lo;
+        if (threadIdx.x < KS)
+            sGen[threadIdx.x] = (threadIdx.x < a.gen_count) ? a.B + threadIdx.x * a.ldb : nullptr;
+    }
+    __syncthreads();
+    if (a.mode == UPD_PLE && a.left_copies) {
+        for (int k = blockIdx.x; k < nS; k += gridDim.x) {
+            const uint64_t *src = a.S + (int64_t)k * a.ldS;
+            uint64_t *dst = a.A + (r + d->S_off[k]) * a.ld;
+            for (int64_t w = threadIdx.x; w < w_lo; w += blockDim.x) dst[w] = src[w];
+            for (int64_t w = W + threadIdx.x; w < a.W_full; w += blockDim.x) dst[w] = src[w];
+        }
+    }
+    const int64_t R = row_hi - row_lo, NW = W - w_lo;
+    if (R <= 0 || NW <= 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.bytes) atomicAdd(a.bytes, (unsigned long long)(R * NW * 16));
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < R * NW;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = row_lo + t / NW, w = w_lo + t % NW;
+        const uint64_t *src = a.A + i * a.ld;
+        if (a.mode == UPD_PLE && i - r <= maxpos) {
+            const int mv = a.map[i];
+            if (mv >= 0 && (mv >> 8) == a.stripe) src = a.S + (int64_t)(mv & 255) * a.ldS;
+        }
+        uint64_t ix = a.idx[i * a.idx_stride];
+        uint64_t x = src[w];
+        while (ix) {
+            const int b = __ffsll((long long)ix) - 1;
+            ix &= ix - 1;
+            if (sGen[b]) x ^= sGen[b][w];
+        }
+        a.A[i * a.ld + w] = x;
+    }
+}
+
 cudaError_t setup_update_kernel()
 {
     const int smem = (int)(TAB_WORDS * sizeof(uint64_t));
@@ -457,6 +528,10 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
     const bool vec = (a.ld % 2 == 0) && ((uintptr_t)a.A % 16 == 0) &&
                      ((a.mode != UPD_PLE && a.mode != UPD_M4RI) || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
     int grid = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
+    if (a.naive && a.mode != UPD_M4RI) {
+        naive_update_kernel<<<8 * num_sms, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     if (vec) {
         grid &= ~1;
         if (grid < 2) grid = 2;

@@ -331,5 +331,25 @@ bool encode_row_tiles(TensorMap2D *out, const uint64_t *A, int64_t m, int64_t W,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Expanded FP4 operand of the own GEMM (kernels_gemm_f4.cu): `rows` rows of
+// `rowb` bytes, boxes of box_rows rows x 128 bytes with the 128-byte swizzle
+// the MMA descriptors expect; the caller pads so that the tensor is at least
+// one box in each dimension.  Out-of-range boxes read zeros.
+bool encode_f4_operand(TensorMap2D *out, const uint8_t *base, int64_t rows, int64_t rowb, int box_rows)
+{
+    if (!out || !base || ((uintptr_t)base & 15u) || (rowb & 15) || rowb < 128 || rows < box_rows ||
+        box_rows < 1 || box_rows > 256 || rows > (int64_t(1) << 31) - 1 || rowb > (int64_t(1) << 31) - 1)
+        return false;
+    const EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)rowb, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)rowb};
+    const cuuint32_t box[2] = {128u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(reinterpret_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(base),
+              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 
 }  // namespace gf2

@@ -116,6 +116,10 @@ extern "C" int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_wor
     int rc = noalloc_setup(dev, &nd);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the scratch address is the current device's: the work must run there
+    int sdev = dev;
+    NA_CK(cudaStreamGetDevice(st, &sdev));
+    if (sdev != dev) return GF2_EINVAL;
 
     char *base = nd->base;
     int64_t *r_dev = reinterpret_cast<int64_t *>(base + OFF_SMALL);

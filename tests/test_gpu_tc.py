@@ -156,3 +156,26 @@ def test_mul_default_large_k_matches_oracle():
     dC = to_dev(np.zeros((m, gi.words_for(n)), np.uint64))
     hh.mul(dC, to_dev(A), to_dev(B), m, k, n)
     assert np.array_equal(to_host(dC), oracle.mul(A, B, m, k, n))
+
+
+@pytest.mark.parametrize("m,n", [(300, 1100), (1000, 1500), (2048, 2048)])
+def test_naive_update_ple_and_rref(m, n):
+    """The plain baseline (GF2_OPT_NAIVE_UPDATE: generator rows added one by
+    one, no tables) gives the same unique PLE and RREF."""
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    hh.set_option(g.OPT_NAIVE_UPDATE, 1)
+    hh.set_option(g.OPT_LOOKAHEAD, 0)
+    A = gi.bernoulli_matrix(m, n, 5 * m + n)
+    dA = to_dev(A)
+    P, Q = vec_dev(m), vec_dev(min(m, n))
+    r = hh.ple(dA, m, n, P, Q)
+    LE = A.copy()
+    r0, P0, Q0 = oracle.ple(LE, m, n)
+    assert r == r0 and np.array_equal(P.cpu().numpy()[:m], P0)
+    assert np.array_equal(to_host(dA, gi.words_for(n)), LE)
+    dR = to_dev(A)
+    assert hh.rref(dR, m, n, Q) == r0
+    R0 = A.copy()
+    oracle.rref(R0, m, n)
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)

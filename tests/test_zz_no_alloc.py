@@ -25,12 +25,22 @@ def _ple_existing(h, A, m, n):
     return r, to_host(dA, gi.words_for(n)), P.cpu().numpy()[:m], Q.cpu().numpy()[:min(m, n)]
 
 
-def _ple_noalloc(A, m, n):
+def _ple_noalloc(A, m, n, ld=None, offset=0):
+    """Run gf2_ple_noalloc on a device copy of A with ld words per row, the
+    matrix starting `offset` words into its buffer (offset 1: a base that is
+    only 8-byte aligned)."""
+    import torch
     import paper_1111_6549_gb300 as g
-    dA = to_dev(A)
+    w = gi.words_for(n)
+    ld = w if ld is None else ld
+    flat = np.zeros(offset + m * ld + 1, dtype=np.uint64)
+    flat[offset:offset + m * ld].reshape(m, ld)[:, :w] = A
+    buf = torch.from_numpy(flat.view(np.int64)).cuda()
+    dA = buf[offset:offset + m * ld].view(m, ld)
     P, Q = vec_dev(m), vec_dev(min(m, n))
     r = g.ple_noalloc(dA, m, n, P, Q)
-    return r, to_host(dA, gi.words_for(n)), P.cpu().numpy()[:m], Q.cpu().numpy()[:min(m, n)]
+    out = dA.cpu().numpy().view(np.uint64)[:, :w]
+    return r, np.ascontiguousarray(out), P.cpu().numpy()[:m], Q.cpu().numpy()[:min(m, n)]
 
 
 def test_noalloc_matches_ple_on_consecutive_calls():
@@ -51,6 +61,23 @@ def test_noalloc_matches_ple_on_consecutive_calls():
             assert np.array_equal(got[2], want[2])
             assert np.array_equal(got[3], want[3])
             assert np.array_equal(got[1], want[1])
+
+
+def test_noalloc_matches_the_oracle_with_odd_and_padded_rows():
+    """Against the CPU oracle directly, with leading dimensions that send the
+    update through its word-by-word form: an odd ld (n = 960, 15 words) and a
+    padded ld with a base that is only 8-byte aligned."""
+    import oracle
+    for m, n, ld, offset in [(960, 960, 15, 0), (1000, 700, 12, 1), (513, 1500, 24, 0)]:
+        A = gi.bernoulli_matrix(m, n, seed=3 * m + n)
+        ref = A.copy()
+        r0, P0, Q0 = oracle.ple(ref, m, n)
+        for _ in range(2):
+            r, out, P, Q = _ple_noalloc(A, m, n, ld, offset)
+            assert r == r0
+            assert np.array_equal(P, P0)
+            assert np.array_equal(Q, Q0)
+            assert np.array_equal(out, ref)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
