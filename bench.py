@@ -397,6 +397,12 @@ def tc_compare(args):
     dev = torch.device("cuda", 0)
     h = g.Handle(0)
     stream = torch.cuda.current_stream(dev)
+    try:
+        h.set_option(g.OPT_MUL_GEMM_FORMAT, 4)
+        lib_gemm = True
+    except g.GF2Error:
+        lib_gemm = False
+    h.set_option(g.OPT_MUL_GEMM_FORMAT, 0)
 
     def timeit(fn, reps=5, pre=None):
         ts = []
@@ -419,21 +425,21 @@ def tc_compare(args):
         B = torch.from_numpy(gi.bernoulli_matrix(k, n, 2).view(np.int64)).to(dev)
         C = torch.zeros((m, gi.words_for(n)), dtype=torch.int64, device=dev)
         res, outs = {"m": m, "k": k, "n": n}, {}
-        for name, tc, gk, fmt in (("table", 0, 0, 8), ("tcgen05", 1, 0, 8), ("fp8_gemm", 0, 1, 8),
-                                  ("fp4_gemm", 0, 1, 4)):
+        forms = [("table", 0, 0, 0), ("tcgen05_smem_expand", 1, 0, 0), ("own_fp4_gemm", 0, 1, 0)]
+        if lib_gemm:
+            forms += [("library_fp8_gemm", 0, 1, 8), ("library_fp4_gemm", 0, 1, 4)]
+        for name, tc, gk, fmt in forms:
             h.set_option(g.OPT_TC_MUL, tc)
             h.set_option(g.OPT_MUL_GEMM_MIN_K, gk)
             h.set_option(g.OPT_MUL_GEMM_FORMAT, fmt)
             res[name + "_ms"] = timeit(lambda: h.mul(C, A, B, m, k, n))
             res[name + "_tera_and_xor_per_s"] = m * k * n / (res[name + "_ms"] / 1e3) / 1e12
             outs[name] = C.clone()
-        res["identical"] = bool(torch.equal(outs["table"], outs["tcgen05"]) and
-                                torch.equal(outs["table"], outs["fp8_gemm"]) and
-                                torch.equal(outs["table"], outs["fp4_gemm"]))
+        res["identical"] = all(bool(torch.equal(outs["table"], v)) for v in outs.values())
         out["mul"].append(res)
     h.set_option(g.OPT_TC_MUL, 0)
     h.set_option(g.OPT_MUL_GEMM_MIN_K, 4096)
-    h.set_option(g.OPT_MUL_GEMM_FORMAT, 4)
+    h.set_option(g.OPT_MUL_GEMM_FORMAT, 0)
     for nn in (16384, 32768):
         A = torch.from_numpy(gi.dense_square(nn).view(np.int64)).to(dev)
         Wk = torch.empty_like(A)
@@ -725,8 +731,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
-    ap.add_argument("--gemm-format", type=int, default=None, choices=(8, 4),
-                    help="operand format of the library GEMM in the blocked products (default: the library's)")
+    ap.add_argument("--gemm-format", type=int, default=None, choices=(0, 8, 4),
+                    help="GF(2) product form in the blocked steps: 0 the own tcgen05 FP4 GEMM (default), "
+                         "4 / 8 the library GEMM (builds with GF2_WITH_CUBLASLT=1 only)")
     ap.add_argument("--rref-block", type=int, default=None,
                     help="base block width of the recursive RREF recovery (0: flat; default: the library's)")
     ap.add_argument("--ple-block", type=int, default=None,

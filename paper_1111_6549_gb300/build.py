@@ -21,6 +21,12 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+# GF2_WITH_CUBLASLT=1 also builds the library-GEMM form of the GF(2) product
+# (GF2_OPT_MUL_GEMM_FORMAT 4 / 8, for comparison); the default build has only
+# the library's own kernels and links no cuBLAS.
+WITH_CUBLASLT = os.environ.get("GF2_WITH_CUBLASLT", "0") == "1"
+if WITH_CUBLASLT:
+    FLAGS = FLAGS + ["-DGF2_WITH_CUBLASLT"]
 
 
 def sources():
@@ -33,6 +39,9 @@ def _deps():
 
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
+        return False
+    stamp = LIB + ".cfg"
+    if not os.path.exists(stamp) or open(stamp).read() != str(WITH_CUBLASLT):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -59,11 +68,13 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 1)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublasLt"]
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + (["-lcublasLt"] if WITH_CUBLASLT else [])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".cfg", "w") as fh:
+        fh.write(str(WITH_CUBLASLT))
     return LIB
 
 

@@ -47,7 +47,7 @@ struct gf2_handle {
     BatchTune btune{};             // batched kernel: table configuration per size class
     bool tma = false;              // update rows move by TMA where A allows it (measured slower)
     int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the library GEMM
-    int gemm_fmt = 4;              // its operand format: 4 = FP4 E2M1 (block scales 1), 8 = FP8 E4M3
+    int gemm_fmt = 0;              // 0: own tcgen05 FP4 GEMM; library GEMM (if built in): 4 = FP4 E2M1, 8 = FP8 E4M3
     int64_t rref_block = -1;       // RREF recovery: base block width of the recursive form (0: flat, -1: auto)
     bool wide_update = true;       // table updates on aligned rows: 128-byte tiles, nine tables
     bool naive_update = false;     // plain baseline: trailing updates as one-by-one row additions
@@ -1499,6 +1499,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
     case GF2_OPT_NAIVE_UPDATE: h->naive_update = value != 0; return GF2_OK;
     case GF2_OPT_MUL_GEMM_FORMAT:
         if (value != 8 && value != 4 && value != 0) return GF2_EINVAL;
+        if (value != 0 && !kLibraryGemm) return GF2_EINVAL;   // library GEMM not built in
         h->gemm_fmt = (int)value;
         return GF2_OK;
     case GF2_OPT_MUL_GEMM_MIN_K:

@@ -166,6 +166,13 @@ cudaError_t launch_expand_transpose(cudaStream_t st, int fmt, const uint64_t *B,
                                     int64_t n, int64_t kp, uint8_t *out, int num_sms);
 cudaError_t launch_parity(cudaStream_t st, const float *D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,
                           int64_t ldc, int num_sms);
+// library GEMM (built only with GF2_WITH_CUBLASLT; otherwise create returns null)
+constexpr bool kLibraryGemm =
+#ifdef GF2_WITH_CUBLASLT
+    true;
+#else
+    false;
+#endif
 void *gemm_lt_create();
 void gemm_lt_destroy(void *g);
 int gemm_counts(void *g, cudaStream_t st, int fmt, const uint8_t *Ax, const uint8_t *Bxt, float *D, int64_t rows,

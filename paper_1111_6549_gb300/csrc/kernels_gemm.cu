@@ -17,7 +17,9 @@
 //     into C (so C accumulates).
 #include "common.cuh"
 
+#ifdef GF2_WITH_CUBLASLT
 #include <cublasLt.h>
+#endif
 
 #include <algorithm>
 #include <new>
@@ -227,6 +229,7 @@ cudaError_t launch_parity(cudaStream_t st, const float *D, int64_t ldd, int64_t 
 
 }  // namespace gf2
 
+#ifdef GF2_WITH_CUBLASLT
 // ---------------------------------------------------------------------------
 // The GEMM: D (rows x n, row-major, ld ldd, fp32) = Ax (rows x kp values,
 // K-major) times Bxt^T (Bxt: n x kp values, K-major), by cuBLASLt.  In
@@ -342,3 +345,19 @@ int gemm_counts(void *p, cudaStream_t st, int fmt, const uint8_t *Ax, const uint
 }
 
 }  // namespace gf2
+
+#else  // library GEMM not built in: the own tcgen05 GEMM (kernels_gemm_f4.cu) is the only one
+
+namespace gf2 {
+
+void *gemm_lt_create() { return nullptr; }
+void gemm_lt_destroy(void *) {}
+int gemm_counts(void *, cudaStream_t, int, const uint8_t *, const uint8_t *, float *, int64_t, int64_t, int64_t,
+                int64_t)
+{
+    return -1;
+}
+
+}  // namespace gf2
+
+#endif

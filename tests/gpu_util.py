@@ -20,3 +20,17 @@ def to_host(t, w: int | None = None) -> np.ndarray:
 def vec_dev(n: int, fill: int = -7):
     import torch
     return torch.full((max(n, 1),), fill, dtype=torch.int64, device="cuda")
+
+
+def library_gemm_available() -> bool:
+    """True when libgf2 was built with the library-GEMM form of the product
+    (GF2_WITH_CUBLASLT=1); the default build has only its own kernels."""
+    import paper_1111_6549_gb300 as g
+    h = g.Handle()
+    try:
+        h.set_option(g.OPT_MUL_GEMM_FORMAT, 4)
+        return True
+    except g.GF2Error:
+        return False
+    finally:
+        h.close()

@@ -9,12 +9,13 @@ import pytest
 import gf2inputs as gi
 import oracle
 from tests.gpu_util import to_dev, to_host, vec_dev
+from tests.gpu_util import library_gemm_available
 from tests.test_gpu_parity import assert_ple_equal, make, ref_ple
 
 pytestmark = pytest.mark.gpu
 
 
-def handle(block, gemm_min_k=None, fmt=8, rref_block=None):
+def handle(block, gemm_min_k=None, fmt=0, rref_block=None):
     import paper_1111_6549_gb300 as g
     h = g.Handle()
     h.set_option(g.OPT_PLE_BLOCK, block)
@@ -42,8 +43,10 @@ def test_blocked_ple_matches_oracle(block, kind, m, n):
     assert_ple_equal(run(handle(block), A, m, n), ref_ple(A, m, n))
 
 
-@pytest.mark.parametrize("gemm_min_k,fmt", [(1, 8), (1, 4), (0, 8)])
+@pytest.mark.parametrize("gemm_min_k,fmt", [(1, 0), (1, 8), (1, 4), (0, 0)])
 def test_blocked_ple_gemm_and_table_products(gemm_min_k, fmt):
+    if fmt and not library_gemm_available():
+        pytest.skip("library GEMM not built in (GF2_WITH_CUBLASLT)")
     """The block's product through the FP8 or FP4 GEMM (min k 1) and through the tables (0)."""
     m, n = 3000, 2049
     A = make("dense", m, n, seed=3)
@@ -101,7 +104,7 @@ def test_blocked_rref_pivot_gaps(dups, rref_block):
     for c in dups:
         U[:, c] = U[:, c - 37]
     A = gi.pack(U, A.shape[1])
-    h = handle(640, 1, 4 if len(dups) % 2 else 8, rref_block)
+    h = handle(640, 1, 0, rref_block)
     dR = to_dev(A)
     Q = vec_dev(n)
     r = h.rref(dR, m, n, Q)
