@@ -77,14 +77,24 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         }
         return;
     }
-    if (warp == 0) panel_window(A, r, ld, cw, rows, keff, sh);
+    if (warp == 0) panel_window_t(A, r, ld, cw, rows, keff, sh);
     __syncthreads();
-    if (sh.fail) panel_block(A, r, ld, cw, rows, keff, gs, sh, fallbacks);
+    const bool fell_back = sh.fail != 0;
+    if (fell_back) panel_block(A, r, ld, cw, rows, keff, gs, sh, fallbacks);
 
     // ---------------- outputs
     const int rbar = sh.rbar;
     __shared__ uint64_t sMinv[KS], sLinv[KS];          // shared copies for the prep tables
-    if (warp == 1) {
+    if (!fell_back) {
+        // the window path left L11^-1 and U11^-1 in shared memory
+        for (int p = tid; p < rbar; p += blockDim.x) {
+            const uint64_t li = sh.Linv[p], mi = sh.Minv[p];
+            d->Linv[p] = li;
+            sLinv[p] = li;
+            d->Minv[p] = mi;
+            sMinv[p] = mi;
+        }
+    } else if (warp == 1) {
         // U11^-1 for the RREF recovery, U11[p][q] = E11[p] at column qbar[q]
         // (unit upper triangular): lane-parallel backward substitution per
         // column, rows collected by ballot.  Runs beside warp 0's L11^-1.
@@ -112,7 +122,7 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
             }
         }
     }
-    if (warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv, sLinv);
+    if (fell_back && warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv, sLinv);
     for (int p = tid; p < rbar; p += blockDim.x) {
         P[r + p] = r + sh.t[p];
         Q[r + p] = c + sh.j[p];
