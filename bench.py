@@ -166,16 +166,63 @@ def oracle_sample(A: np.ndarray, m: int, n: int, pivots: int, threads: int):
     return w, dt, k
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(A: np.ndarray, m: int, n: int, target_s: float = 12.0):
+    """The CPU oracle on the bench's host: a bounded sample of the same
+    workload on every core, plus single-threaded timings -- the full 2048^2
+    RREF (median of 3) and the first pivot steps of the 32768^2 elimination
+    over its full width, extrapolated by the work count to the whole
+    elimination."""
+    import gf2inputs as gi
+    import oracle
     threads = os.cpu_count() or 1
     w1, dt1, k1 = oracle_sample(A, m, n, 32, threads)
     per = dt1 / max(k1, 1)
     piv = int(max(64, min(8192, target_s / max(per, 1e-6))))
     w, dt, k = oracle_sample(A, m, n, piv, threads)
+    # single thread: 2048^2 RREF via PLE, three runs
+    A2 = gi.dense_square(2048)
+    t2 = []
+    for _ in range(3):
+        B = A2.copy()
+        t0 = time.perf_counter()
+        r2, _ = oracle.rref(B, 2048, 2048, threads=1)
+        t2.append(time.perf_counter() - t0)
+    ms2 = statistics.median(t2) * 1e3
+    # single thread: 32768^2, first pivot steps for about 4 s
+    A3 = gi.dense_square(32768)
+    wa, da, ka = oracle_sample(A3, 32768, 32768, 8, 1)
+    pv = int(max(16, min(4096, 4.0 / max(da / max(ka, 1), 1e-6))))
+    ws_, ds_, ks_ = oracle_sample(A3, 32768, 32768, pv, 1)
+    rate1 = ws_ / ds_
+    full = sum((32768 - p) * (32768 - p) for p in range(32768))
     return {"value": w / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {k} pivot steps of the eager oracle elimination of the same "
                       f"{m}x{n} matrix over its full width ({dt:.1f} s); W = sum_p (m-p)(n-p)",
-            "seconds": dt}
+            "seconds": dt, "cpu_model": cpu_model(), "nproc": threads,
+            "single_thread": {
+                "rref_2048_ms_median_of_3": ms2, "rank_2048": int(r2),
+                "rref_2048_gbitops": work_bits(2048, 2048, int(r2)) / (ms2 / 1e3) / 1e9,
+                "elim_32768_sample": f"first {ks_} pivot steps of the 32768x32768 elimination ({ds_:.1f} s)",
+                "elim_32768_gbitops": rate1 / 1e9,
+                "elim_32768_estimated_s": full / rate1}}
 
 
 def run_reference(args):
@@ -324,12 +371,58 @@ def bench_sparse(h, torch, dev, stream, weights=(1, 10, 40, 200), n=10000):
     return out
 
 
-def bench_served(h, torch, dev, rates=(200, 1000, 5000), jobs_per_rate=400, pool_size=48, slots=6):
+class BusySampler:
+    """nvidia-smi utilization.gpu (percent of time a kernel ran) sampled every
+    100 ms while active; median and mean of the samples."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = os.path.join("/tmp", f"gf2_util_{os.getpid()}.csv")
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", "--query-gpu=utilization.gpu",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        vals = []
+        for line in open(self.path):
+            try:
+                vals.append(float(line.strip()))
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        return {"median_pct": statistics.median(vals), "mean_pct": sum(vals) / len(vals),
+                "samples": len(vals)} if vals else None
+
+
+def bench_served(h, torch, dev, rates=(100, 300, 1000, 3000, 10000, 20000), seconds=2.0, max_jobs=2000,
+                 plain_jobs=300, pool_size=48, slots=6):
     """The served solve workload: Poisson arrivals of gf2_solve jobs (n
     log-uniform in 128..16384, 1..64 right-hand sides) through the
-    continuous-batching server, against the plain path (one job at a time
-    through one handle) on the same arrivals.  Inputs come from a pool of
-    pre-generated jobs reused in arrival order."""
+    continuous-batching server at each offered rate, `seconds` of arrivals
+    (at least 200 and at most max_jobs jobs), against the plain path (one job
+    at a time through one handle) on the first plain_jobs arrivals.  Inputs
+    come from a pool of pre-generated jobs reused in arrival order.  The GPU's
+    busy fraction is sampled during each served run; the knee is the highest
+    offered rate the server still keeps up with (jobs/s >= 90 % of it)."""
     import gf2inputs as gi
     import paper_1111_6549_gb300 as g
     pool = []
@@ -342,27 +435,29 @@ def bench_served(h, torch, dev, rates=(200, 1000, 5000), jobs_per_rate=400, pool
         pool.append((n, nrhs, Ap, Bp, Xp))
     max_n = max(p[0] for p in pool)
     out = {"workload": "Poisson arrivals of solve jobs, n log-uniform 128..16384, nrhs U{1..64}",
-           "slots": slots, "pool": pool_size, "rates": []}
+           "slots": slots, "pool": pool_size, "seconds_per_rate": seconds, "rates": []}
     srv = g.Server(slots=slots, max_n=max_n, max_nrhs=64)
-    # device buffers for the plain path
     dA = torch.empty((max_n, gi.words_for(max_n)), dtype=torch.int64, device=dev)
     dB = torch.empty((max_n, 1), dtype=torch.int64, device=dev)
+    q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))]
     for rate in rates:
-        arr = gi.solve_stream_recipe(jobs_per_rate, rate=float(rate), seed=gi.BASE_SEED + 4 + rate)
-        t0 = g.Server.clock() + 0.01
-        for k, jb in enumerate(arr):
-            n, nrhs, Ap, Bp, Xp = pool[k % pool_size]
-            while g.Server.clock() < t0 + jb["t"]:
-                pass
-            srv.submit(k, Ap, n, Bp, nrhs, Xp)
-        srv.drain()
-        res = srv.poll(jobs_per_rate + 8)
+        jobs = int(min(max_jobs, max(200, rate * seconds)))
+        arr = gi.solve_stream_recipe(jobs, rate=float(rate), seed=gi.BASE_SEED + 4 + rate)
+        with BusySampler(dev.index or 0) as busy:
+            t0 = g.Server.clock() + 0.01
+            for k, jb in enumerate(arr):
+                n, nrhs, Ap, Bp, Xp = pool[k % pool_size]
+                while g.Server.clock() < t0 + jb["t"]:
+                    pass
+                srv.submit(k, Ap, n, Bp, nrhs, Xp)
+            srv.drain()
+        res = srv.poll(jobs + 8)
         lat = sorted((r[5] - r[3]) * 1e3 for r in res)
         span = max(r[5] for r in res) - min(r[3] for r in res)
-        # plain path: one job at a time, same arrivals
+        # plain path: one job at a time, same arrivals, the first plain_jobs of them
         lat_p, t_first, t_last = [], None, None
         t0 = g.Server.clock() + 0.01
-        for k, jb in enumerate(arr):
+        for k, jb in enumerate(arr[:plain_jobs]):
             n, nrhs, Ap, Bp, Xp = pool[k % pool_size]
             ta = t0 + jb["t"]
             while g.Server.clock() < ta:
@@ -378,13 +473,16 @@ def bench_served(h, torch, dev, rates=(200, 1000, 5000), jobs_per_rate=400, pool
             t_last = g.Server.clock()
             lat_p.append((t_last - ta) * 1e3)
         lat_p.sort()
-        q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))]
         out["rates"].append({"rate_per_s": rate, "jobs": len(res),
                              "served": {"p50_ms": q(lat, 0.5), "p99_ms": q(lat, 0.99),
-                                        "jobs_per_s": len(res) / span},
-                             "plain": {"p50_ms": q(lat_p, 0.5), "p99_ms": q(lat_p, 0.99),
+                                        "jobs_per_s": len(res) / span, "gpu_busy": busy.summary()},
+                             "plain": {"jobs": len(lat_p), "p50_ms": q(lat_p, 0.5), "p99_ms": q(lat_p, 0.99),
                                        "jobs_per_s": len(lat_p) / (t_last - t_first)}})
     srv.close()
+    keep = [r["rate_per_s"] for r in out["rates"] if r["served"]["jobs_per_s"] >= 0.9 * r["rate_per_s"]]
+    out["knee_rate_per_s"] = max(keep) if keep else None
+    out["capacity_jobs_per_s"] = max(r["served"]["jobs_per_s"] for r in out["rates"])
+    out["plain_capacity_jobs_per_s"] = max(r["plain"]["jobs_per_s"] for r in out["rates"])
     return out
 
 
@@ -571,21 +669,30 @@ def run_ours(args):
     roofline["update_share_of_step_diagnostic"] = (roofline["kernel_ms_per_step_diagnostic"]["update"] /
                                                    per_step_ms) if per_step_ms > 0 else None
 
-    # ---- the plain path: one stripe after another, no look-ahead (same work)
-    plain_ms = None
+    # ---- the plain paths: (a) the same kernels one stripe after another, no
+    # look-ahead; (b) the naive baseline -- one panel per launch and the
+    # trailing updates as one-by-one row additions (no tables, no blocked
+    # products, no look-ahead)
+    plain_ms = naive_ms = None
     if rank == 0 and args.side:
-        h.set_option(g.OPT_LOOKAHEAD, 0)
-        pts = []
-        for _ in range(2):
+        def once():
             work.copy_(pristine)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             step()
             b.record(stream)
             torch.cuda.synchronize()
-            pts.append(a.elapsed_time(b))
+            return a.elapsed_time(b)
+        h.set_option(g.OPT_LOOKAHEAD, 0)
+        plain_ms = min(once() for _ in range(2))
+        h.set_option(g.OPT_NAIVE_UPDATE, 1)
+        h.set_option(g.OPT_PLE_BLOCK, 0)
+        h.set_option(g.OPT_RREF_BLOCK, 0)
+        naive_ms = once()
+        h.set_option(g.OPT_NAIVE_UPDATE, 0)
+        h.set_option(g.OPT_PLE_BLOCK, -1 if args.ple_block is None else args.ple_block)
+        h.set_option(g.OPT_RREF_BLOCK, -1 if args.rref_block is None else args.rref_block)
         h.set_option(g.OPT_LOOKAHEAD, 1)
-        plain_ms = min(pts)
 
     # ---- 32768^2 side measurement (same path, a few steps)
     side = {}
@@ -687,7 +794,8 @@ def run_ours(args):
         sparse = bench_sparse(h, torch, dev, stream)
     served = None
     if rank == 0 and not args.no_serve:
-        served = bench_served(h, torch, dev)
+        served = bench_served(h, torch, dev, seconds=args.served_seconds, slots=args.served_slots,
+                              max_jobs=int(1000 * args.served_seconds))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -705,12 +813,18 @@ def run_ours(args):
                                  "before each step",
                            "seconds_per_step": max_ms / args.steps / 1e3,
                            "ple_only_ms": ple_ms, "m4ri_rref_ms": m4ri_ms, "side_32768": side,
-                           "plain_path_ms": plain_ms,
-                           "speedup_vs_plain_path": (plain_ms / (max_ms / args.steps)) if plain_ms else None,
-                           "plain_path": "same kernels, one stripe after another on one stream "
-                                         "(no look-ahead), one launch per panel step"},
+                           "plain_path_ms": naive_ms,
+                           "speedup_vs_plain_path": (naive_ms / (max_ms / args.steps)) if naive_ms else None,
+                           "plain_path": "naive baseline: one panel per launch per 64-column stripe, trailing "
+                                         "updates as one-by-one row additions (no tables, no blocked products, "
+                                         "no look-ahead)",
+                           "no_lookahead_ms": plain_ms},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "served": served,
                 "sparse": sparse,
+                "rref_65536_ms": max_ms / args.steps if n == 65536 else None,
+                "ple_65536_ms": ple_ms if n == 65536 else None,
+                "rref_32768_ms": side.get("rref_ms"), "ple_32768_ms": side.get("ple_ms"),
+                "m4ri_32768_ms": side.get("m4ri_rref_ms"),
                 "gpu_launches": st["kernel_launches"], "clocks": clk.summary(),
                 "panel_fallbacks": st["panel_fallbacks"], "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
@@ -731,6 +845,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=2.0,
+                    help="seconds of Poisson arrivals per offered rate in the served sweep (30: the full sweep)")
+    ap.add_argument("--served-slots", type=int, default=6, help="execution slots of the solve server")
     ap.add_argument("--gemm-format", type=int, default=None, choices=(0, 8, 4),
                     help="GF(2) product form in the blocked steps: 0 the own tcgen05 FP4 GEMM (default), "
                          "4 / 8 the library GEMM (builds with GF2_WITH_CUBLASLT=1 only)")

@@ -122,9 +122,11 @@ int gf2_rref_m4ri_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, 
  *   C must not overlap A or B.  Asynchronous.
  * Inner dimensions below GF2_OPT_MUL_GEMM_MIN_K (default 4096) use the
  * tabulated row combinations, 64 columns of A per pass over C; larger ones
- * the exact FP4 (or FP8) GEMM (see the options); GF2_OPT_TC_MUL selects the
- * library's own tcgen05 kernel instead.  The GEMM path holds up to about
- * 1 GiB of fp32 counts plus the expanded operands in the handle's workspace.
+ * the library's own block-scaled FP4 tcgen05 GEMM (TMA-fed, parities taken
+ * from tensor memory in its epilogue); GF2_OPT_TC_MUL selects the older
+ * tcgen05 kernel that expands the bits in shared memory.  The GEMM path
+ * holds the operands expanded to FP4 (half a byte per bit; B^T whole, A in
+ * blocks of up to 32768 rows) in the handle's workspace.
  */
 int gf2_mul(gf2_handle_t handle, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda,
             const uint64_t *B, int64_t ldb, int64_t m, int64_t k, int64_t n, int accumulate);
@@ -307,10 +309,10 @@ int gf2_server_destroy(gf2_server_t server);
  *                      where the matrix allows it (16-byte aligned base, even
  *                      ld_words, at least 16 words and 256 rows)
  *   GF2_OPT_MUL_GEMM_MIN_K  gf2_mul with an inner dimension k >= value (0:
- *                      never) runs as an exact low-precision GEMM: the
- *                      library's own kernels expand the bits to FP4 (or FP8)
- *                      0/1, a plain cuBLASLt GEMM counts in fp32, and the
- *                      library takes the parities; below it, the
+ *                      never) runs as an exact tensor-core GEMM: the bits
+ *                      expanded to FP4 0/1, the library's own tcgen05
+ *                      block-scaled FP4 kernel counting in tensor memory and
+ *                      XORing each count's parity into C; below it, the
  *                      Four-Russians tables (default 4096)
  *   GF2_OPT_PLE_BLOCK  value > 0 (a multiple of 64): PLE (and everything
  *                      built on it) decomposes value columns at a time with
@@ -321,12 +323,14 @@ int gf2_server_destroy(gf2_server_t server);
  *                      the host then reads the rank once per block, so the
  *                      _async calls wait for each block's pivot search;
  *                      0: one table update per 64-column stripe; -1
- *                      (default): blocks of half the pivot columns from
- *                      65536 pivot columns on, else 0
- *   GF2_OPT_MUL_GEMM_FORMAT  operand format of that GEMM: 4 = FP4 E2M1
- *                      with every 16-value block scale 1.0 (NVFP4 form, the
- *                      FP4 tensor rate; default), 8 = FP8 E4M3; the counts
- *                      are exact either way
+ *                      (default): blocks of 16384 columns from 65536 pivot
+ *                      columns on, else 0.  The block's TRSM halves down to
+ *                      1024-row leaves, each solved by one fused launch
+ *   GF2_OPT_MUL_GEMM_FORMAT  0 (default): the library's own FP4 GEMM;
+ *                      4 / 8: a cuBLASLt GEMM on FP4 E2M1 (NVFP4 scales
+ *                      1.0) / FP8 E4M3 operands followed by a parity pass,
+ *                      only in a library built with GF2_WITH_CUBLASLT=1
+ *                      (GF2_EINVAL otherwise); the counts are exact always
  *   GF2_OPT_RREF_BLOCK value > 0 (a multiple of 64): the RREF recovery
  *                      (gf2_rref, gf2_solve) halves the pivot stripes
  *                      recursively down to blocks of value columns: the
@@ -335,7 +339,7 @@ int gf2_server_destroy(gf2_server_t server);
  *                      product through gf2_mul, then the left half follows;
  *                      the table passes run only inside the blocks.  0: one
  *                      table pass per stripe over all rows above it; -1
- *                      (default): blocks of 16384 columns from 65536 pivot
+ *                      (default): blocks of 8192 columns from 32768 pivot
  *                      columns on, else 0
  *   GF2_OPT_WIDE_UPDATE the table updates on 16-byte aligned rows take
  *                      128-byte column tiles with nine tables per stripe
@@ -346,11 +350,17 @@ int gf2_server_destroy(gf2_server_t server);
  *                      update (PLE stripes, RREF passes, table products) adds
  *                      the selected generator rows one by one, with no
  *                      tables; for measuring what the tables buy
+ *   GF2_OPT_PDL        launch the library's kernels with programmatic
+ *                      dependent launch: each kernel is scheduled while the
+ *                      one before it on the stream still runs and waits on
+ *                      the device for its completion, which hides the launch
+ *                      latency between the many short dependent kernels
+ *                      (default on; 0: plain stream ordering)
  * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
  * GF2_EINVAL for an unknown option, a negative value, or a format other
- * than 8 or 4.
+ * than 0, 4 or 8.
  */
 #define GF2_OPT_LOOKAHEAD       1
 #define GF2_OPT_TC_MUL          2
@@ -362,6 +372,7 @@ int gf2_server_destroy(gf2_server_t server);
 #define GF2_OPT_RREF_BLOCK      8
 #define GF2_OPT_WIDE_UPDATE     9
 #define GF2_OPT_NAIVE_UPDATE    10
+#define GF2_OPT_PDL             11
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */
@@ -380,12 +391,20 @@ typedef struct gf2_stats {
     int64_t update_timed_launches;/* update launches timed while profiling     */
 } gf2_stats;
 /* Per-launch event timing: 0 off, 1 the update kernel only, 2 every kernel,
-   3 every 7th update launch (only those add to update_ms and update_bytes).
-   While profiling is off update_bytes counts every update launch. */
+   3 every 7th update launch (only those add to update_ms and update_bytes),
+   4 every kernel and a timeline (gf2_get_timeline).  While profiling is off
+   update_bytes counts every update launch. */
 int gf2_set_profiling(gf2_handle_t handle, int on);
 /* Read the counters (synchronises the stream to finish the event timing). */
 int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);
 int gf2_reset_stats(gf2_handle_t handle);
+/* Profiling level 4: the timed launches since the last reset, in launch
+   order, as (kind, start ms, end ms) triples in out (host, 3 * max_records
+   doubles); kind 0 update, 1 panel, 2 prep, 3 RREF prep, 4 other; times from
+   CUDA events recorded on each launch's stream, relative to the first one.
+   *count = the number of records (more than max_records: the rest are not
+   written).  Synchronises the stream. */
+int gf2_get_timeline(gf2_handle_t handle, double *out, int64_t max_records, int64_t *count);
 
 /*
  * Tensor-core carriers of a GF(2) product (Section 3.3: the block step of

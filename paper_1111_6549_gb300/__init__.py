@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
 (OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE, OPT_TMA_UPDATE, OPT_MUL_GEMM_MIN_K, OPT_PLE_BLOCK,
- OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE, OPT_NAIVE_UPDATE) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
+ OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE, OPT_NAIVE_UPDATE, OPT_PDL) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11
 BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
 CARRIER_B1, CARRIER_FP4, CARRIER_FP8 = 1, 4, 8
@@ -123,6 +123,7 @@ def load():
             "gf2_server_clock": ([], ctypes.c_double),
             "gf2_server_destroy": ([vp], ctypes.c_int),
             "gf2_carrier_check": ([ctypes.c_int, vp, vp, vp], ctypes.c_int),
+            "gf2_get_timeline": ([vp, ctypes.POINTER(ctypes.c_double), i64, i64p], ctypes.c_int),
             "gf2_carrier_rate": ([ctypes.c_int, i64, ctypes.POINTER(ctypes.c_double), i64p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -342,13 +343,23 @@ class Handle:
     # ---- statistics -----------------------------------------------------
     def set_profiling(self, level) -> None:
         """0: off, 1 (or True): time the update kernel, 2: time every kernel,
-        3: time every 7th update launch (only those count in update_ms/update_bytes)."""
+        3: time every 7th update launch (only those count in update_ms/update_bytes),
+        4: time every kernel and keep a timeline (Handle.timeline)."""
         _check(load().gf2_set_profiling(self._h, int(level)), "gf2_set_profiling")
 
     def stats(self) -> dict:
         s = _Stats()
         _check(load().gf2_get_stats(self._h, ctypes.byref(s)), "gf2_get_stats")
         return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+    def timeline(self):
+        """Profiling level 4: [(kind, start_ms, end_ms), ...] of the timed launches."""
+        L = load()
+        cnt = ctypes.c_int64(0)
+        _check(L.gf2_get_timeline(self._h, None, 0, ctypes.byref(cnt)), "gf2_get_timeline")
+        buf = (ctypes.c_double * (3 * max(cnt.value, 1)))()
+        _check(L.gf2_get_timeline(self._h, buf, cnt.value, ctypes.byref(cnt)), "gf2_get_timeline")
+        return [(int(buf[3 * i]), buf[3 * i + 1], buf[3 * i + 2]) for i in range(cnt.value)]
 
     def reset_stats(self) -> None:
         _check(load().gf2_reset_stats(self._h), "gf2_reset_stats")

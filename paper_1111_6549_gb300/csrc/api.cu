@@ -18,6 +18,10 @@
 #include <utility>
 #include <vector>
 
+namespace gf2 {
+thread_local bool g_pdl = false;
+}  // namespace gf2
+
 using namespace gf2;
 
 struct gf2_handle {
@@ -44,6 +48,8 @@ struct gf2_handle {
     struct Pending { cudaEvent_t e0, e1; int kind; };
     std::vector<Pending> ev_pending;
     double kind_ms[5] = {0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other
+    cudaEvent_t tl_ref = nullptr;  // profiling level 4: the timeline's time origin (first timed event)
+    std::vector<double> timeline;  // level 4: (kind, start ms, end ms) per timed launch
     BatchTune btune{};             // batched kernel: table configuration per size class
     bool tma = false;              // update rows move by TMA where A allows it (measured slower)
     int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the library GEMM
@@ -51,9 +57,12 @@ struct gf2_handle {
     int64_t rref_block = -1;       // RREF recovery: base block width of the recursive form (0: flat, -1: auto)
     bool wide_update = true;       // table updates on aligned rows: 128-byte tiles, nine tables
     bool naive_update = false;     // plain baseline: trailing updates as one-by-one row additions
+    bool pdl = true;               // launches with programmatic dependent launch (GF2_OPT_PDL)
     int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
     char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
     size_t lbuf_cap = 0;
+    char *tbuf = nullptr;          // blocked PLE: indices of the fused TRSM leaf
+    size_t tbuf_cap = 0;
     void *lt = nullptr;            // cuBLASLt state (created on first use)
     char *gbuf = nullptr;          // expanded operands and fp32 counts of the GEMM path
     size_t gbuf_cap = 0;
@@ -62,6 +71,12 @@ struct gf2_handle {
     int64_t tm_m = -1, tm_W = -1, tm_ld = -1;
     bool tm_ok = false;
 };
+
+// the own tensor-core product (defined with the C entry points below)
+extern "C" {
+static int mul_own(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,
+                   int64_t ldb, int64_t m, int64_t k, int64_t n);
+}
 
 namespace {
 
@@ -113,6 +128,14 @@ Layout layout_for(int64_t m, int64_t ncols)
     L.total = off;
     return L;
 }
+
+// GF2_OPT_PDL for the launches of one call (restored on exit, so nested
+// calls keep the outer setting)
+struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool on) : prev(g_pdl) { g_pdl = on; }
+    ~PdlScope() { g_pdl = prev; }
+};
 
 struct DeviceGuard {
     int prev = -1;
@@ -168,7 +191,7 @@ struct Timed {
     Timed(gf2_handle *h_, int kind_, cudaStream_t st_ = nullptr, bool enable = true)
         : h(h_), kind(kind_), st(st_ ? st_ : h_->stream)
     {
-        if (!enable || h->profiling == 0 || (h->profiling != 2 && kind != K_UPDATE)) return;
+        if (!enable || h->profiling == 0 || (h->profiling != 2 && h->profiling != 4 && kind != K_UPDATE)) return;
         e0 = take();
         if (e0) cudaEventRecord(e0, st);
     }
@@ -195,10 +218,11 @@ struct Timed {
 // the timed steps while the ratio bytes / time still covers the whole run.
 constexpr int64_t UPD_SAMPLE = 7;
 
-int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
+int launch_update_counted(gf2_handle *h, const UpdArgs &a_in, cudaStream_t st = nullptr)
 {
+    if (!st) st = h->stream;
     const bool timed = h->profiling != 3 || h->upd_launches % UPD_SAMPLE == 0;
-    Timed t(h, K_UPDATE, nullptr, timed);
+    Timed t(h, K_UPDATE, st, timed);
     UpdArgs a = a_in;
     if (!timed) a.bytes = nullptr;
     else if (h->profiling) h->upd_timed += 1;
@@ -218,8 +242,8 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in)
         }
         if (h->tm_ok) a.tmap = &h->tmap;
     }
-    if (tc) CK(launch_update_tc(h->stream, a, h->num_sms));
-    else CK(launch_update(h->stream, a, h->num_sms));
+    if (tc) CK(launch_update_tc(st, a, h->num_sms));
+    else CK(launch_update(st, a, h->num_sms));
     h->launches += 1;
     h->upd_launches += 1;
     return GF2_OK;
@@ -261,21 +285,27 @@ int run_ple_range(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         }
         h->launches += 1;
     }
-    auto panel = [&](cudaStream_t st, int64_t s) -> int {
+    // launches that follow a wait on another stream's event take no PDL
+    // attribute, so that the event keeps its full ordering
+    // resolve: the previous stripe's update may still be running (its moved
+    // rows are read from its staged copies)
+    auto panel = [&](cudaStream_t st, int64_t s, bool resolve) -> int {
+        PdlScope no_pdl(g_pdl && st == h->stream);
         Timed t(h, K_PANEL, st);
         CK(launch_panel(st, A, m, ld, npiv, (int)s, descs, r_dev(h), P, Q, map_of(s), gs, fb_dev(h),
-                        ptab_of(s)));
+                        ptab_of(s), resolve ? map_of(s - 1) : nullptr, S, L.ldS));
         h->launches += 1;
         return GF2_OK;
     };
-    auto prep = [&](int64_t s) -> int {
+    auto prep = [&](int64_t s, int64_t nw) -> int {
         Timed t(h, K_PREP);
         CK(launch_prep(h->stream, A, m, ld, W, (int)s, descs, map_of(s), S, L.ldS, IDX, err_dev(h),
-                       ptab_of(s), h->num_sms));
+                       ptab_of(s), h->num_sms, nw));
         h->launches += 1;
         return GF2_OK;
     };
-    auto upd = [&](int64_t s, int64_t tp_lo, int64_t tp_hi, int left, int grid) -> int {
+    auto upd = [&](int64_t s, int64_t tp_lo, int64_t tp_hi, int left, int grid, int first_off = 1,
+                   cudaStream_t ust = nullptr) -> int {
         UpdArgs a{};
         a.mode = UPD_PLE;
         a.A = A;
@@ -295,7 +325,8 @@ int run_ple_range(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         a.tp_hi = tp_hi;
         a.left_copies = left;
         a.grid = grid;
-        return launch_update_counted(h, a);
+        a.first_off = first_off;
+        return launch_update_counted(h, a, ust);
     };
     UpdArgs probe{};
     probe.mode = UPD_PLE;
@@ -307,31 +338,42 @@ int run_ple_range(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
                     h->num_sms >= 8;
     if (!la) {
         for (int64_t s = s_lo; s < s_hi; ++s) {
-            if ((rc = panel(h->stream, s))) return rc;
-            if ((rc = prep(s))) return rc;
+            if ((rc = panel(h->stream, s, false))) return rc;
+            if ((rc = prep(s, -1))) return rc;
             if ((rc = upd(s, 0, -1, 1, 0))) return rc;
         }
         return GF2_OK;
     }
-    // Look-ahead: U1(s) updates the first tile pair (which holds stripe s+1)
-    // and the staged rows' left parts; the panel of stripe s+1 then runs on
-    // the side stream while U2(s) updates the remaining tile pairs on all
-    // but two SMs; prep(s+1) waits for both.
+    // Look-ahead: prep(s) also applies stripe s's update to the next stripe's
+    // word of every row, so the panel of stripe s+1 runs right after it on the
+    // main stream, reading the rows stripe s moved from their staged copies,
+    // while the update of stripe s (from the word after that one, on all but
+    // two SMs) runs on the side stream; prep(s+1) waits for both.  The chain
+    // prep -> panel -> prep that bounds narrow trailing blocks thus stays on
+    // one stream.
     CK(cudaEventRecord(h->ev_fork, h->stream));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-    if ((rc = panel(h->stream, s_lo))) return rc;
-    if ((rc = prep(s_lo))) return rc;
+    if ((rc = panel(h->stream, s_lo, false))) return rc;
     for (int64_t s = s_lo; s < s_hi; ++s) {
+        if (s > s_lo) CK(cudaStreamWaitEvent(h->stream, h->ev_p, 0));   // the update of stripe s - 1
         if (s + 1 < s_hi) {
-            if ((rc = upd(s, 0, 1, 1, 0))) return rc;
+            {
+                PdlScope no_pdl(g_pdl && s == s_lo);       // prep(s > s_lo) follows a wait on the update
+                if ((rc = prep(s, s + 1))) return rc;
+            }
             CK(cudaEventRecord(h->ev_u1, h->stream));
             CK(cudaStreamWaitEvent(h->side, h->ev_u1, 0));
-            if ((rc = panel(h->side, s + 1))) return rc;
+            {
+                PdlScope no_pdl(false);
+                if ((rc = upd(s, 0, -1, 1, h->num_sms - 2, 2, h->side))) return rc;
+            }
             CK(cudaEventRecord(h->ev_p, h->side));
-            if ((rc = upd(s, 1, -1, 0, h->num_sms - 2))) return rc;
-            CK(cudaStreamWaitEvent(h->stream, h->ev_p, 0));
-            if ((rc = prep(s + 1))) return rc;
+            if ((rc = panel(h->stream, s + 1, true))) return rc;
         } else {
+            {
+                PdlScope no_pdl(g_pdl && s == s_lo);
+                if ((rc = prep(s, -1))) return rc;
+            }
             if ((rc = upd(s, 0, -1, 1, 0))) return rc;
         }
     }
@@ -341,52 +383,31 @@ int run_ple_range(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
 // X <- L^-1 X for the kb rows X = A[row0 .. row0+kb), words [w_lo, W), with
 // L the unit lower triangular kb x kb matrix whose strictly lower bits are the
 // gathered rows Lt (kb x ldt words, aligned).  Large blocks split in halves
-// (X2 ^= L21 X1 through gf2_mul between the two half solves); from 2048 rows
-// down, 64 pivots at a time: the 64 x 64 diagonal inverse, then one table
-// pass over the rows below.
+// (X2 ^= L21 X1 through the GEMM between the two half solves); from 1024
+// rows down, one fused leaf launch (kernels_blocked.cu: 64-row steps, each CTA
+// owning two words of every row) after one launch that forms its indices.
 static int trsm_lower(gf2_handle *h, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
                       int64_t ldt, int64_t w_lo, int64_t W, int64_t ncols)
 {
-    if (kb > 2048) {
+    if (kb > TRSM_LEAF_ROWS) {
         const int64_t hh = ((kb / 2) + 63) & ~int64_t(63);
         int rc = trsm_lower(h, A, ld, row0, hh, Lt, ldt, w_lo, W, ncols);
         if (rc) return rc;
-        rc = gf2_mul(h, A + (row0 + hh) * ld + w_lo, ld, Lt + hh * ldt, ldt, A + row0 * ld + w_lo, ld, kb - hh, hh,
-                     ncols - 64 * w_lo, 1);
+        // the product always through the tensor-core GEMM: even at the
+        // smallest split (k = TRSM_LEAF_ROWS) it beats 64-row table passes
+        rc = mul_own(h, A + (row0 + hh) * ld + w_lo, ld, Lt + hh * ldt, ldt, A + row0 * ld + w_lo, ld, kb - hh, hh,
+                     ncols - 64 * w_lo);
         if (rc) return rc;
         return trsm_lower(h, A, ld, row0 + hh, kb - hh, Lt + hh * ldt + hh / 64, ldt, w_lo, W, ncols);
     }
-    const int64_t kw = words_for(kb);
-    for (int64_t t = 0; t < kw; ++t) {
-        const int nt = (int)std::min<int64_t>(64, kb - 64 * t);
-        {
-            Timed tt(h, K_OTHER);
-            CK(launch_trsm_diag(h->stream, A, ld, row0 + 64 * t, nt, Lt, ldt, t, w_lo, W, h->num_sms));
-        }
-        h->launches += 1;
-        if (64 * (t + 1) < kb) {
-            UpdArgs a{};
-            a.tp_lo = 0;
-            a.tp_hi = -1;
-            a.left_copies = 1;
-            a.mode = UPD_MUL;
-            a.A = A + row0 * ld;                            // rows relative to row0
-            a.ld = ld;
-            a.m = kb;
-            a.W = W;
-            a.idx = Lt + t;
-            a.idx_stride = ldt;
-            a.B = A + (row0 + 64 * t) * ld;
-            a.ldb = ld;
-            a.gen_count = nt;
-            a.row_lo = 64 * (t + 1);
-            a.row_hi = kb;
-            a.w_lo = w_lo;
-            a.bytes = bytes_dev(h);
-            int rc = launch_update_counted(h, a);
-            if (rc) return rc;
-        }
+    const size_t need = (size_t)kb * (size_t)words_for(kb) * 8;
+    int rc = grow(&h->tbuf, &h->tbuf_cap, need, h->stream);
+    if (rc) return rc;
+    {
+        Timed t(h, K_OTHER);
+        CK(launch_trsm_leaf(h->stream, A, ld, row0, kb, Lt, ldt, reinterpret_cast<uint64_t *>(h->tbuf), w_lo, W));
     }
+    h->launches += 2;
     return GF2_OK;
 }
 
@@ -402,10 +423,11 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
             int64_t *Q)
 {
     const int64_t W = words_for(ncols), ns = words_for(npiv);
-    // stripes per block; automatic: one split in the middle from 65536 pivot
-    // columns on (measured on GB300: 65536^2 PLE 120 ms against 129 ms per
-    // stripe; at 32768^2 the per-stripe form is faster)
-    const int64_t bs = h->ple_block >= 0 ? h->ple_block / 64 : (npiv >= 65536 ? (ns + 1) / 2 : 0);
+    // stripes per block; automatic: blocks of 16384 columns from 65536 pivot
+    // columns on (measured on GB300 with the own GEMM and the fused TRSM
+    // leaves: 65536^2 PLE 75.1 ms against 83.6 ms with two blocks and 97 ms
+    // per stripe; at 32768^2 blocking does not pay)
+    const int64_t bs = h->ple_block >= 0 ? h->ple_block / 64 : (npiv >= 65536 ? 256 : 0);
     if (bs <= 0 || ns <= bs) return run_ple_range(h, A, m, ncols, ld, npiv, P, Q, 0, ns, W, true);
     int64_t r0 = 0;
     for (int64_t s0 = 0; s0 < ns; s0 += bs) {
@@ -490,6 +512,16 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         a.idx = IDX;
         a.idx_stride = 1;
         a.bytes = bytes_dev(h);
+        // the pipelined table kernel leaves the skipped words out within one
+        // launch; the other forms take the two word ranges one after another
+        a.skip_lo = 0;
+        a.skip_hi = 0;
+        if (split && skip_hi < W && update_vectorised(a) && !h->tc_update && !h->tma && !h->naive_update) {
+            a.W = W;
+            a.skip_lo = skip_lo;
+            a.skip_hi = skip_hi;
+            return launch_update_counted(h, a);
+        }
         int rc = launch_update_counted(h, a);
         if (rc || !split || skip_hi >= W) return rc;
         a.W = W;
@@ -505,8 +537,11 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
     // through gf2_mul -- and recurses into the left half.  Table passes and
     // products skip the words from stripe b's first column up to the first
     // column at or after it that is no pivot: zero in every row involved.
+    // automatic: base blocks of 8192 columns from 32768 pivot columns on
+    // (measured on GB300: 65536^2 RREF step 105.7 ms against 108.1 ms with
+    // 16384-column blocks; 32768^2 faster than the flat recovery)
     const int64_t base = h->rref_block > 0 ? h->rref_block / 64
-                                           : (h->rref_block < 0 && npiv >= 65536 ? 256 : 0);
+                                           : (h->rref_block < 0 && npiv >= 32768 ? 128 : 0);
     if (base > 0 && ns > base) {
         int64_t r = 0;
         CK(cudaMemcpyAsync(&r, r_dev(h), sizeof(r), cudaMemcpyDeviceToHost, h->stream));
@@ -716,6 +751,7 @@ int gf2_destroy(gf2_handle_t h)
 {
     if (!h) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     cudaStreamSynchronize(h->stream);
     for (auto &p : h->ev_pending) { cudaEventDestroy(p.e0); cudaEventDestroy(p.e1); }
     for (auto e : h->ev_free) cudaEventDestroy(e);
@@ -728,6 +764,7 @@ int gf2_destroy(gf2_handle_t h)
     cudaFree(h->bws);
     cudaFree(h->gbuf);
     cudaFree(h->lbuf);
+    cudaFree(h->tbuf);
     gemm_lt_destroy(h->lt);
     cudaFree(h->small);
     delete h;
@@ -757,6 +794,7 @@ int gf2_ple_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld,
     if (m > 0 && n > 0 && !Q) return GF2_EINVAL;
     if (!rank_dev) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     if (m == 0 || n == 0) {
         if (m > 0) CK(launch_init_ple(h->stream, P, Q, m, 0, nullptr, r_dev(h), h->num_sms));
         else CK(cudaMemsetAsync(r_dev(h), 0, 8, h->stream));
@@ -776,6 +814,7 @@ int gf2_ple(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int64
     if (rc) return rc;
     if (!rank || (m > 0 && !P) || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     *rank = 0;
     if (m == 0) return GF2_OK;
     if (n == 0) {
@@ -806,6 +845,7 @@ int gf2_rref(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, int6
     if (rc) return rc;
     if (!rank || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     *rank = 0;
     if (m == 0 || n == 0) return GF2_OK;
     rc = rref_enqueue(h, A, m, n, ld, Q);
@@ -821,6 +861,7 @@ int gf2_rref_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld
     if (rc) return rc;
     if (!rank_dev || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     if (m == 0 || n == 0) {
         CK(cudaMemsetAsync(rank_dev, 0, 8, h->stream));
         return GF2_OK;
@@ -838,6 +879,7 @@ int gf2_rref_m4ri(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld,
     if (rc) return rc;
     if (!rank || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     *rank = 0;
     if (m == 0 || n == 0) return GF2_OK;
     rc = run_m4ri(h, A, m, n, ld, Q);
@@ -853,6 +895,7 @@ int gf2_rref_m4ri_async(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64
     if (rc) return rc;
     if (!rank_dev || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     if (m == 0 || n == 0) {
         CK(cudaMemsetAsync(rank_dev, 0, 8, h->stream));
         return GF2_OK;
@@ -980,6 +1023,7 @@ int gf2_mul(gf2_handle_t h, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t
     if (!C || ldc < words_for(n)) return GF2_EINVAL;
     if (k > 0 && (!A || !B || lda < words_for(k) || ldb < words_for(n))) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     const int64_t Wc = words_for(n);
     if (!accumulate)
         CK(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)Wc * 8, (size_t)m, h->stream));
@@ -1074,6 +1118,7 @@ int gf2_solve_async(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_
     if (!status_dev || nrhs < 0) return GF2_EINVAL;
     if (n > 0 && nrhs > 0 && (!B || ldb < words_for(nrhs))) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     if (n == 0) {
         CK(cudaMemsetAsync(status_dev, 0, sizeof(int32_t), h->stream));
         return GF2_OK;
@@ -1089,6 +1134,7 @@ int gf2_solve(gf2_handle_t h, uint64_t *A, int64_t n, int64_t lda, uint64_t *B, 
     if (!solve_status || nrhs < 0) return GF2_EINVAL;
     if (n > 0 && nrhs > 0 && (!B || ldb < words_for(nrhs))) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     *solve_status = GF2_SOLVE_UNIQUE;
     if (n == 0) return GF2_OK;
     int32_t *status_dev = reinterpret_cast<int32_t *>(h->small + SM_STATUS);
@@ -1189,6 +1235,7 @@ int gf2_ple_batched(gf2_handle_t h, const gf2_desc *descs, int64_t count)
     int rc = check_batch(h, descs, count);
     if (rc) return rc;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     const BatchSplit b = split_batch(descs, count);
     if (!b.small.empty()) {
         const BatchBuf L = batch_buf(h->num_sms, count, b);
@@ -1234,6 +1281,7 @@ int gf2_batched_autotune(gf2_handle_t h, int reps, double *ms_out)
 {
     if (!h || reps < 1 || reps > 100) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     int rc = finish_sync(h);
     if (rc) return rc;
     const int grid = batched_grid(h->num_sms);
@@ -1357,6 +1405,7 @@ int gf2_batched_plan_create(gf2_handle_t h, const gf2_desc *descs, int64_t count
     const BatchSplit b = split_batch(descs, count);
     if (!b.large.empty()) return GF2_EINVAL;       // plans hold only the persistent launch
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     gf2_batched_plan *p = new (std::nothrow) gf2_batched_plan();
     if (!p) return GF2_ENOMEM;
     p->h = h;
@@ -1421,6 +1470,7 @@ int gf2_ple_host(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld, 
     if (rc) return rc;
     if (!rank || (m > 0 && !P) || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     *rank = 0;
     if (m == 0) return GF2_OK;
     const int64_t qn = std::min(m, n);
@@ -1452,6 +1502,7 @@ int gf2_rref_host(gf2_handle_t h, uint64_t *A, int64_t m, int64_t n, int64_t ld,
     if (rc) return rc;
     if (!rank || (m > 0 && n > 0 && !Q)) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     *rank = 0;
     if (m == 0 || n == 0) return GF2_OK;
     const int64_t qn = std::min(m, n);
@@ -1474,6 +1525,7 @@ int gf2_selftest_wait(gf2_handle_t h, int64_t limit_us)
 {
     if (!h || limit_us < 0 || limit_us > 1000000) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     CK(launch_wait_selftest(h->stream, err_dev(h), (unsigned long long)limit_us * 1000ull));
     h->launches += 1;
     return finish_sync(h);
@@ -1497,6 +1549,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
         return GF2_OK;
     case GF2_OPT_WIDE_UPDATE: h->wide_update = value != 0; return GF2_OK;
     case GF2_OPT_NAIVE_UPDATE: h->naive_update = value != 0; return GF2_OK;
+    case GF2_OPT_PDL: h->pdl = value != 0; return GF2_OK;
     case GF2_OPT_MUL_GEMM_FORMAT:
         if (value != 8 && value != 4 && value != 0) return GF2_EINVAL;
         if (value != 0 && !kLibraryGemm) return GF2_EINVAL;   // library GEMM not built in
@@ -1513,7 +1566,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
 int gf2_set_profiling(gf2_handle_t h, int on)
 {
     if (!h) return GF2_EINVAL;
-    h->profiling = on < 0 ? 0 : (on > 3 ? 3 : on);
+    h->profiling = on < 0 ? 0 : (on > 4 ? 4 : on);
     return GF2_OK;
 }
 
@@ -1521,12 +1574,25 @@ int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
 {
     if (!h || !out) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     CK(cudaStreamSynchronize(h->stream));
     for (auto &p : h->ev_pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) h->kind_ms[p.kind] += ms;
         else cudaGetLastError();
-        h->ev_free.push_back(p.e0);
+        if (h->profiling == 4) {
+            float t0 = 0.f, t1 = 0.f;
+            if (!h->tl_ref) h->tl_ref = p.e0;           // kept as the origin until the next reset
+            if (cudaEventElapsedTime(&t0, h->tl_ref, p.e0) == cudaSuccess &&
+                cudaEventElapsedTime(&t1, h->tl_ref, p.e1) == cudaSuccess) {
+                h->timeline.push_back((double)p.kind);
+                h->timeline.push_back((double)t0);
+                h->timeline.push_back((double)t1);
+            } else {
+                cudaGetLastError();
+            }
+        }
+        if (p.e0 != h->tl_ref) h->ev_free.push_back(p.e0);
         h->ev_free.push_back(p.e1);
     }
     h->ev_pending.clear();
@@ -1547,13 +1613,29 @@ int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
     return GF2_OK;
 }
 
+int gf2_get_timeline(gf2_handle_t h, double *out, int64_t max_records, int64_t *count)
+{
+    if (!h || !count || max_records < 0 || (max_records > 0 && !out)) return GF2_EINVAL;
+    gf2_stats st;
+    const int rc = gf2_get_stats(h, &st);                 // resolves the pending events
+    if (rc) return rc;
+    const int64_t n = (int64_t)h->timeline.size() / 3;
+    *count = n;
+    const int64_t k = std::min(n, max_records);
+    for (int64_t i = 0; i < 3 * k; ++i) out[i] = h->timeline[(size_t)i];
+    return GF2_OK;
+}
+
 int gf2_reset_stats(gf2_handle_t h)
 {
     if (!h) return GF2_EINVAL;
     DeviceGuard g(h->device);
+    PdlScope pdl_scope(h->pdl);
     CK(cudaStreamSynchronize(h->stream));
     for (auto &p : h->ev_pending) { h->ev_free.push_back(p.e0); h->ev_free.push_back(p.e1); }
     h->ev_pending.clear();
+    if (h->tl_ref) { h->ev_free.push_back(h->tl_ref); h->tl_ref = nullptr; }
+    h->timeline.clear();
     h->launches = 0;
     h->upd_launches = 0;
     h->upd_timed = 0;

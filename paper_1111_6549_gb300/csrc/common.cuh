@@ -9,7 +9,41 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace gf2 {
+
+// ---- programmatic dependent launch (PDL)
+// A kernel of this library starts with pdl_wait() -- it returns once the
+// kernel launched before it on the stream has completed and its memory
+// operations are visible (at once when there is none, or when the kernel was
+// launched without the attribute) -- and pdl_trigger(), which lets the next
+// kernel on the stream be scheduled while this one runs (its CTAs then sit in
+// their own pdl_wait()).  Only the waiting is needed for correctness; the
+// early scheduling hides the launch latency between dependent kernels.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// Launches made by the calling thread carry the PDL attribute while this is
+// set (the handle's GF2_OPT_PDL, set for the duration of each call).
+extern thread_local bool g_pdl;
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args &&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = g_pdl ? attr : nullptr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 constexpr int KS = 64;            // stripe width in columns (one uint64 word)
 constexpr int SMAX = 2 * KS;      // rows staged per stripe: pivot rows + displaced rows
@@ -113,6 +147,9 @@ struct UpdArgs {
     int64_t W_full;            // PLE: row width; staged rows also get words [W, W_full) (0: none)
     int wide;                  // aligned rows: 128-byte tiles with nine tables (else paired 64-byte tiles)
     int naive;                 // plain baseline: generator rows added one by one, no tables
+    int first_off;             // PLE: first updated word = stripe word + first_off (0: 1)
+    int64_t skip_lo, skip_hi;  // words [skip_lo, skip_hi) may be left out (zero in every row
+                               // involved); only the pipelined table kernel uses it
 };
 
 // A CUtensorMap (128 bytes) kept opaque outside the files that use TMA.
@@ -131,12 +168,18 @@ cudaError_t launch_init_ple(cudaStream_t st, int64_t *P, int64_t *Q, int64_t m, 
 // words, PREP_TAB_BYTES) in ptab when it is not null; the PLE's prep reads them.
 constexpr int PREP_TAB_WORDS = 8 * 256;
 constexpr size_t PREP_TAB_BYTES = 3 * PREP_TAB_WORDS * sizeof(uint64_t);
+// prev_map / prev_S (may be null): the previous stripe's row map and staged
+// rows, read for the rows its swaps moved while its update may still run.
 cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t npiv, int s,
                          StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
-                         PanelScratch gs, int32_t *fallbacks, uint64_t *ptab);
+                         PanelScratch gs, int32_t *fallbacks, uint64_t *ptab, const int32_t *prev_map = nullptr,
+                         const uint64_t *prev_S = nullptr, int64_t ldS = 0);
+// next_word >= 0: the prep also applies the stripe's update to that word of
+// every row (the next stripe's word, for its panel to start early; the
+// update kernel then starts one word later, UpdArgs::first_off = 2).
 cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
                         StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
-                        uint64_t *IDX, int32_t *err, const uint64_t *ptab, int num_sms);
+                        uint64_t *IDX, int32_t *err, const uint64_t *ptab, int num_sms, int64_t next_word = -1);
 cudaError_t setup_update_kernel();
 cudaError_t setup_prep_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
@@ -185,8 +228,11 @@ cudaError_t launch_gather_pivbits(cudaStream_t st, const uint64_t *A, int64_t ld
                                   int num_sms);
 cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *descs, int s0,
                                     int s1, int64_t w_lo, int64_t W);
-cudaError_t launch_trsm_diag(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int nt, const uint64_t *Lt,
-                             int64_t ldt, int64_t t, int64_t w_lo, int64_t W, int num_sms);
+// fused TRSM leaf (kb <= TRSM_LEAF_ROWS): indices into Lp (kb * ceil(kb / 64)
+// words), then one launch over the words [w_lo, W)
+cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
+                             int64_t ldt, uint64_t *Lp, int64_t w_lo, int64_t W);
+constexpr int64_t TRSM_LEAF_ROWS = 1024;
 cudaError_t launch_wait_selftest(cudaStream_t st, int32_t *err, unsigned long long limit_ns);
 cudaError_t launch_m4ri_prep(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *G,

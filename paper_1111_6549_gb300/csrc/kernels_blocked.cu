@@ -10,9 +10,9 @@
 //     U = L11^-1 A[r0:r1, right]               (TRSM, pivot rows)
 //     A[r1:m, right] ^= L21 U                   (product, rows below)
 // gather_lbits_kernel copies the L bits [r0, r1) of rows r0.. into an aligned
-// buffer (the GEMM and TRSM operands), trsm_diag_kernel applies the inverse
-// of one 64 x 64 unit lower diagonal block of L11 to its 64 rows; the rest is
-// the table update (UPD_MUL) and gf2_mul.
+// buffer (the GEMM and TRSM operands); the TRSM halves recursively through
+// gf2_mul down to leaves of at most 4096 rows, each solved by one fused launch
+// (trsm_leaf_kernel).
 #include "panel_dev.cuh"
 
 namespace gf2 {
@@ -22,6 +22,8 @@ namespace gf2 {
 __global__ void gather_lbits_kernel(const uint64_t *__restrict__ A, int64_t ld, int64_t W, int64_t row0,
                                     int64_t rows, int64_t c0, int64_t kb, int64_t kw, uint64_t *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t total = rows * kw;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -44,8 +46,8 @@ cudaError_t launch_gather_lbits(cudaStream_t st, const uint64_t *A, int64_t ld, 
     int64_t blocks = (rows * kw + 255) / 256;
     if (blocks > 8 * num_sms) blocks = 8 * num_sms;
     if (blocks < 1) blocks = 1;
-    gather_lbits_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, W, row0, rows, c0, kb, kw, out);
-    return cudaGetLastError();
+    return launch_kernel(gather_lbits_kernel, dim3((int)blocks), dim3(256), 0, st, A, ld, W, row0, rows, c0, kb, kw,
+                         out);
 }
 
 // out[i][w] = the bits of row row0 + i at the columns Qb[64 w .. 64 w + 64)
@@ -56,6 +58,8 @@ __global__ void gather_pivbits_kernel(const uint64_t *__restrict__ A, int64_t ld
                                       int64_t rows, const int64_t *__restrict__ Qb, int64_t kb, int64_t kw,
                                       uint64_t *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t total = rows * kw;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -87,50 +91,153 @@ cudaError_t launch_gather_pivbits(cudaStream_t st, const uint64_t *A, int64_t ld
     int64_t blocks = (rows * kw + 255) / 256;
     if (blocks > 8 * num_sms) blocks = 8 * num_sms;
     if (blocks < 1) blocks = 1;
-    gather_pivbits_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, W, row0, rows, Qb, kb, kw, out);
-    return cudaGetLastError();
+    return launch_kernel(gather_pivbits_kernel, dim3((int)blocks), dim3(256), 0, st, A, ld, W, row0, rows, Qb, kb, kw,
+                         out);
 }
 
-constexpr int TRSM_THREADS = 256;
+// ---------------------------------------------------------------------------
+// Fused TRSM leaf: X <- L^-1 X for the kb <= TRSM_LEAF_ROWS rows X = A[row0 ..
+// row0 + kb) over the words [w_lo, W), L unit lower triangular with its
+// strictly lower bits gathered in Lt (kb x ldt words).  Forward substitution
+// in steps of 64 rows: step t replaces rows 64 t .. 64 t + 63 by their
+// product with the inverse of L's diagonal block t and adds to every row
+// below its L bits in block t times those new rows.  Both are one table
+// lookup per row on tables built from the step's rows as they stand before
+// the step (the index of a diagonal row p is row p of the block inverse
+// plus e_p; of a row below, its L bits times the block inverse), so a whole
+// leaf is one launch: columns are independent, each CTA owns two words of
+// every row and walks all steps alone.  trsm_leaf_prep_kernel forms the
+// indices, one CTA per step.
 
-// Rows X[0 .. nt) (X = A + row0 * ld) <- Linv X over the words [w_lo, W),
-// Linv the inverse of the unit lower nt x nt block whose strictly lower bits
-// are Lblk[p] (word t of the gathered L rows 64 t + p).
-__global__ void __launch_bounds__(TRSM_THREADS)
-trsm_diag_kernel(uint64_t *A, int64_t ld, int64_t row0, int nt, const uint64_t *__restrict__ Lt, int64_t ldt,
-                 int64_t t, int64_t w_lo, int64_t W)
+constexpr int LEAF_THREADS = 256;
+
+// Lp[t * kb + i] for the rows i >= 64 t of the leaf: the index of row i in
+// step t (as above).
+__global__ void __launch_bounds__(LEAF_THREADS)
+trsm_leaf_prep_kernel(const uint64_t *__restrict__ Lt, int64_t ldt, int64_t kb, uint64_t *__restrict__ Lp)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint64_t sL[KS], sM[KS];
-    __shared__ uint64_t sIn[KS][4];
-    const int tid = threadIdx.x;
-    if (tid < KS) sL[tid] = (tid < nt) ? (Lt[(64 * t + tid) * ldt + t] & ((1ull << tid) - 1ull)) : 0ull;
+    __shared__ uint64_t tab[8][256];
+    const int t = blockIdx.x, tid = threadIdx.x;
+    const int nt = (int)min((int64_t)KS, kb - 64 * (int64_t)t);
+    if (tid < KS) sL[tid] = (tid < nt) ? (Lt[(64 * (int64_t)t + tid) * ldt + t] & ((1ull << tid) - 1ull)) : 0ull;
     __syncthreads();
     if (tid < 32) warp_lower_inverse(sL, nt, sM);
     __syncthreads();
-    const int p = tid >> 2, wq = tid & 3;
-    for (int64_t wb = w_lo + (int64_t)blockIdx.x * 4; wb < W; wb += (int64_t)gridDim.x * 4) {
-        const int64_t w = wb + wq;
-        sIn[p][wq] = (p < nt && w < W) ? A[(row0 + p) * ld + w] : 0ull;
-        __syncthreads();
-        if (p < nt && w < W) {
-            const uint64_t mrow = sM[p];
-            uint64_t acc = 0;
-            for (int q = 0; q < nt; ++q)
-                if ((mrow >> q) & 1ull) acc ^= sIn[q][wq];
-            A[(row0 + p) * ld + w] = acc;
+    // byte tables of the block inverse's rows: tab[b][e] = XOR of rows 8 b + q, bits q of e
+    for (int e2 = tid; e2 < 8 * 256; e2 += blockDim.x) {
+        const int b = e2 >> 8, e = e2 & 255;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (((e >> q) & 1) && 8 * b + q < nt) acc ^= sM[8 * b + q];
+        tab[b][e] = acc;
+    }
+    __syncthreads();
+    const uint64_t vmask = nt == 64 ? ~0ull : ((1ull << nt) - 1ull);
+    for (int64_t i = 64 * (int64_t)t + tid; i < kb; i += blockDim.x) {
+        const int64_t off = i - 64 * (int64_t)t;
+        uint64_t v;
+        if (off < nt) {
+            v = sM[off] ^ (1ull << off);
+        } else {
+            const uint64_t x = Lt[i * ldt + t] & vmask;
+            v = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) v ^= tab[b][(x >> (8 * b)) & 255u];
         }
-        __syncthreads();
+        Lp[(int64_t)t * kb + i] = v;
     }
 }
 
-cudaError_t launch_trsm_diag(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int nt, const uint64_t *Lt,
-                             int64_t ldt, int64_t t, int64_t w_lo, int64_t W, int num_sms)
+// One CTA per pair of words; see the comment above.
+__global__ void __launch_bounds__(LEAF_THREADS)
+trsm_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *__restrict__ Lp, int64_t w_lo,
+                 int64_t W)
 {
-    int64_t blocks = (W - w_lo + 3) / 4;
-    if (blocks > 2 * num_sms) blocks = 2 * num_sms;
-    if (blocks < 1) blocks = 1;
-    trsm_diag_kernel<<<(int)blocks, TRSM_THREADS, 0, st>>>(A, ld, row0, nt, Lt, ldt, t, w_lo, W);
-    return cudaGetLastError();
+    pdl_wait();
+    pdl_trigger();
+    __shared__ __align__(16) uint64_t T[8 * 256 * 2];      // eight 8-bit tables of 16-byte entries
+    __shared__ uint64_t G[KS][2];
+    const int tid = threadIdx.x;
+    const int64_t w0 = w_lo + 2 * (int64_t)blockIdx.x;
+    if (w0 >= W) return;
+    const bool two = w0 + 1 < W;
+    uint64_t *X = A + row0 * ld + w0;
+    const int nsteps = (int)((kb + 63) / 64);
+    for (int t = 0; t < nsteps; ++t) {
+        const int64_t r0 = 64 * (int64_t)t;
+        const int nt = (int)min((int64_t)KS, kb - r0);
+        __syncthreads();                                   // rows of this step written by the last one
+        if (tid < 2 * KS) {
+            const int p = tid >> 1, q = tid & 1;
+            G[p][q] = (p < nt && (q == 0 || two)) ? X[(r0 + p) * ld + q] : 0ull;
+        }
+        __syncthreads();
+        if (tid < 128) {
+            // table tau (rows 8 tau .. 8 tau + 7), 32-entry segment sg, word q:
+            // Gray-code walk from the segment's base entry
+            const int q = tid & 1, sg = (tid >> 1) & 7, tau = tid >> 4;
+            uint64_t g[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) g[b] = G[8 * tau + b][q];
+            uint64_t val = ((sg & 1) ? g[5] : 0ull) ^ ((sg & 2) ? g[6] : 0ull) ^ ((sg & 4) ? g[7] : 0ull);
+            uint64_t *Tt = T + (tau * 256 + 32 * sg) * 2 + q;
+            int x = 0;
+            Tt[0] = val;
+#pragma unroll
+            for (int i = 1; i < 32; ++i) {
+                const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4;
+                x ^= 1 << b;
+                val ^= g[b];
+                Tt[x * 2] = val;
+            }
+        }
+        __syncthreads();
+        const uint64_t *Lpt = Lp + (int64_t)t * kb;
+        for (int64_t i0 = r0 + tid; i0 < kb; i0 += 4 * LEAF_THREADS) {
+            uint64_t ix[4], x0[4], x1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + (int64_t)u * LEAF_THREADS;
+                ix[u] = 0;
+                x0[u] = 0;
+                x1[u] = 0;
+                if (i < kb) {
+                    ix[u] = __ldg(Lpt + i);
+                    x0[u] = X[i * ld];
+                    if (two) x1[u] = X[i * ld + 1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + (int64_t)u * LEAF_THREADS;
+                if (i >= kb) continue;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const ulonglong2 tv =
+                        *reinterpret_cast<const ulonglong2 *>(T + (b * 256 + ((ix[u] >> (8 * b)) & 255u)) * 2);
+                    x0[u] ^= tv.x;
+                    x1[u] ^= tv.y;
+                }
+                X[i * ld] = x0[u];
+                if (two) X[i * ld + 1] = x1[u];
+            }
+        }
+    }
+}
+
+cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
+                             int64_t ldt, uint64_t *Lp, int64_t w_lo, int64_t W)
+{
+    if (kb <= 0 || kb > TRSM_LEAF_ROWS || w_lo >= W) return cudaSuccess;
+    cudaError_t e =
+        launch_kernel(trsm_leaf_prep_kernel, dim3((int)((kb + 63) / 64)), dim3(LEAF_THREADS), 0, st, Lt, ldt, kb, Lp);
+    if (e != cudaSuccess) return e;
+    return launch_kernel(trsm_leaf_kernel, dim3((int)((W - w_lo + 1) / 2)), dim3(LEAF_THREADS), 0, st, A, ld, row0,
+                         kb, (const uint64_t *)Lp, w_lo, W);
 }
 
 constexpr int PERM_CHUNK = 8;                          // words per CTA
@@ -143,6 +250,8 @@ constexpr int PERM_THREADS = 256;
 __global__ void __launch_bounds__(PERM_THREADS)
 permute_trailing_kernel(uint64_t *A, int64_t ld, const StripeDesc *descs, int s0, int s1, int64_t w_lo, int64_t W)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint64_t tmp[SMAX][PERM_CHUNK];
     const int64_t wb = w_lo + (int64_t)blockIdx.x * PERM_CHUNK;
     if (wb >= W) return;
@@ -170,8 +279,8 @@ cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, co
 {
     const int64_t blocks = (W - w_lo + PERM_CHUNK - 1) / PERM_CHUNK;
     if (blocks <= 0 || s1 <= s0) return cudaSuccess;
-    permute_trailing_kernel<<<(int)blocks, PERM_THREADS, 0, st>>>(A, ld, descs, s0, s1, w_lo, W);
-    return cudaGetLastError();
+    return launch_kernel(permute_trailing_kernel, dim3((int)blocks), dim3(PERM_THREADS), 0, st, A, ld, descs, s0, s1,
+                         w_lo, W);
 }
 
 }  // namespace gf2

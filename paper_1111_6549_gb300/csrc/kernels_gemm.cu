@@ -112,6 +112,8 @@ template <int FMT>
 __global__ void expand_rows_kernel(const uint64_t *__restrict__ A, int64_t lda, int64_t rows, int64_t k0,
                                    int64_t k, int64_t kp, uint8_t *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t rb = kp * FMT / 8;                   // bytes per output row
     const int64_t wpr = kp >> 6;                       // words per output row
     const int64_t total = rows * wpr;
@@ -136,6 +138,8 @@ template <int FMT>
 __global__ void expand_transpose_kernel(const uint64_t *__restrict__ B, int64_t ldb, int64_t k0, int64_t k,
                                         int64_t n, int64_t kp, uint8_t *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t rb = kp * FMT / 8;
     const int lane = threadIdx.x & 31;
     const int64_t nbk = kp >> 6, nbn = (n + 63) >> 6;
@@ -195,11 +199,8 @@ cudaError_t launch_expand_rows(cudaStream_t st, int fmt, const uint64_t *A, int6
     int64_t blocks = (total + 255) / 256;
     if (blocks > 16 * num_sms) blocks = 16 * num_sms;
     if (blocks < 1) blocks = 1;
-    if (fmt == 4)
-        expand_rows_kernel<4><<<(int)blocks, 256, 0, st>>>(A, lda, rows, k0, k, kp, out);
-    else
-        expand_rows_kernel<8><<<(int)blocks, 256, 0, st>>>(A, lda, rows, k0, k, kp, out);
-    return cudaGetLastError();
+    if (fmt == 4) return launch_kernel(expand_rows_kernel<4>, dim3((int)blocks), dim3(256), 0, st, A, lda, rows, k0, k, kp, out);
+    return launch_kernel(expand_rows_kernel<8>, dim3((int)blocks), dim3(256), 0, st, A, lda, rows, k0, k, kp, out);
 }
 
 cudaError_t launch_expand_transpose(cudaStream_t st, int fmt, const uint64_t *B, int64_t ldb, int64_t k0, int64_t k,
@@ -210,10 +211,8 @@ cudaError_t launch_expand_transpose(cudaStream_t st, int fmt, const uint64_t *B,
     if (blocks > 16 * num_sms) blocks = 16 * num_sms;
     if (blocks < 1) blocks = 1;
     if (fmt == 4)
-        expand_transpose_kernel<4><<<(int)blocks, 256, 0, st>>>(B, ldb, k0, k, n, kp, out);
-    else
-        expand_transpose_kernel<8><<<(int)blocks, 256, 0, st>>>(B, ldb, k0, k, n, kp, out);
-    return cudaGetLastError();
+        return launch_kernel(expand_transpose_kernel<4>, dim3((int)blocks), dim3(256), 0, st, B, ldb, k0, k, n, kp, out);
+    return launch_kernel(expand_transpose_kernel<8>, dim3((int)blocks), dim3(256), 0, st, B, ldb, k0, k, n, kp, out);
 }
 
 cudaError_t launch_parity(cudaStream_t st, const float *D, int64_t ldd, int64_t rows, int64_t n, uint64_t *C,

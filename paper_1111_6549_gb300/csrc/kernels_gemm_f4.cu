@@ -139,6 +139,8 @@ __device__ __forceinline__ void g_tile(int64_t t, int64_t TM, int64_t TN, int64_
 __global__ void __launch_bounds__(G_THREADS, 1)
     gemm_f4_kernel(const __grid_constant__ TensorMap2D tmA, const __grid_constant__ TensorMap2D tmB, GemmF4Args a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(1024) uint8_t g_smem[];
     uint8_t *stages = g_smem + ((1024u - (smem_u32(g_smem) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(stages + G_STAGES * G_STAGE_BYTES);
@@ -314,8 +316,7 @@ cudaError_t launch_gemm_f4(cudaStream_t st, uint64_t *C, int64_t ldc, const uint
     GemmF4Args a{C, ldc, m, n, (rowb + G_KB - 1) / G_KB, err};
     const int64_t tiles = ((m + G_BM - 1) / G_BM) * ((n + G_BN - 1) / G_BN);
     const int grid = (int)std::min<int64_t>(num_sms, std::max<int64_t>(tiles, 1));
-    gemm_f4_kernel<<<grid, G_THREADS, G_SMEM, st>>>(ta, tb, a);
-    return cudaGetLastError();
+    return launch_kernel(gemm_f4_kernel, dim3(grid), dim3(G_THREADS), G_SMEM, st, ta, tb, a);
 }
 
 }  // namespace gf2

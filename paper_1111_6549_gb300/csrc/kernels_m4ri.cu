@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(M4P_THREADS)
 m4ri_prep_kernel(const uint64_t *A, int64_t ld, int64_t W, int s, const StripeDesc *descs, const int32_t *map,
                  uint64_t *S, int64_t ldS, uint64_t *G, uint64_t *IDX, int64_t m, int nbg, int nbs)
 {
+    pdl_wait();
+    pdl_trigger();
     const StripeDesc *d = descs + s;
     const int rbar = d->rbar;
     if (rbar == 0) return;
@@ -96,9 +98,8 @@ cudaError_t launch_m4ri_prep(cudaStream_t st, const uint64_t *A, int64_t ld, int
     const int nbs = 16;
     int nbi = (int)std::min<int64_t>(2 * num_sms, (m + M4P_THREADS - 1) / M4P_THREADS);
     if (nbi < 1) nbi = 1;
-    m4ri_prep_kernel<<<nbg + nbs + nbi, M4P_THREADS, 0, st>>>(A, ld, W, s, descs, map, S, ldS, G, IDX, m, nbg,
-                                                               nbs);
-    return cudaGetLastError();
+    return launch_kernel(m4ri_prep_kernel, dim3(nbg + nbs + nbi), dim3(M4P_THREADS), 0, st, A, ld, W, s, descs, map, S,
+                         ldS, G, IDX, m, nbg, nbs);
 }
 
 }  // namespace gf2

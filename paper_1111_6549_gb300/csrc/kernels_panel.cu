@@ -37,6 +37,8 @@ namespace gf2 {
 __global__ void init_ple_kernel(int64_t *P, int64_t *Q, int64_t m, int64_t qn, int32_t *map,
                                 int64_t *r_dev)
 {
+    pdl_wait();
+    pdl_trigger();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (i == 0) *r_dev = 0;
@@ -53,15 +55,17 @@ cudaError_t launch_init_ple(cudaStream_t st, int64_t *P, int64_t *Q, int64_t m, 
     int64_t blocks = (m + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 8 * num_sms) blocks = 8 * num_sms;
-    init_ple_kernel<<<(int)blocks, 256, 0, st>>>(P, Q, m, qn, map, r_dev);
-    return cudaGetLastError();
+    return launch_kernel(init_ple_kernel, dim3((int)blocks), dim3(256), 0, st, P, Q, m, qn, map, r_dev);
 }
 
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv, int s,
              StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
-             PanelScratch gs, int32_t *fallbacks, uint64_t *ptab)
+             PanelScratch gs, int32_t *fallbacks, uint64_t *ptab, const int32_t *prev_map,
+             const uint64_t *prev_S, int64_t ldS)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ PanelShared sh;
     StripeDesc *d = descs + s;
     const int64_t r = *r_dev;
@@ -77,24 +81,26 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         }
         return;
     }
-    if (warp == 0) panel_window_t(A, r, ld, cw, rows, keff, sh);
+    // with the previous stripe's update still running, the rows its swaps
+    // moved are read from its staged copies
+    PrevStage ps{nullptr, prev_S, ldS, 0, -1, s - 1};
+    if (prev_map && s > 0) {
+        const StripeDesc *dp = descs + (s - 1);
+        if (dp->rbar > 0) {
+            ps.map = prev_map;
+            ps.r = dp->r;
+            ps.maxpos = dp->maxpos;
+        }
+    }
+    if (warp < 4) panel_window4(A, r, ld, cw, rows, keff, sh, ps);
     __syncthreads();
     const bool fell_back = sh.fail != 0;
-    if (fell_back) panel_block(A, r, ld, cw, rows, keff, gs, sh, fallbacks);
+    if (fell_back) panel_block(A, r, ld, cw, rows, keff, gs, sh, fallbacks, ps);
 
     // ---------------- outputs
     const int rbar = sh.rbar;
     __shared__ uint64_t sMinv[KS], sLinv[KS];          // shared copies for the prep tables
-    if (!fell_back) {
-        // the window path left L11^-1 and U11^-1 in shared memory
-        for (int p = tid; p < rbar; p += blockDim.x) {
-            const uint64_t li = sh.Linv[p], mi = sh.Minv[p];
-            d->Linv[p] = li;
-            sLinv[p] = li;
-            d->Minv[p] = mi;
-            sMinv[p] = mi;
-        }
-    } else if (warp == 1) {
+    if (warp == 1) {
         // U11^-1 for the RREF recovery, U11[p][q] = E11[p] at column qbar[q]
         // (unit upper triangular): lane-parallel backward substitution per
         // column, rows collected by ballot.  Runs beside warp 0's L11^-1.
@@ -102,7 +108,9 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         for (int p = lane; p < rbar; p += 32) {
             const uint64_t e = sh.E[p];
             uint64_t u = 0;
-            for (int q = 0; q < rbar; ++q) u |= ((e >> sh.j[q]) & 1ull) << q;
+#pragma unroll 16
+            for (int q = 0; q < KS; ++q)
+                u |= (q < rbar ? ((e >> (sh.j[q] & 63)) & 1ull) : 0ull) << q;
             sU[p] = u;
         }
         __syncwarp();
@@ -122,7 +130,7 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
             }
         }
     }
-    if (fell_back && warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv, sLinv);
+    if (warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv, sLinv);
     for (int p = tid; p < rbar; p += blockDim.x) {
         P[r + p] = r + sh.t[p];
         Q[r + p] = c + sh.j[p];
@@ -185,11 +193,11 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
 
 cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t npiv, int s,
                          StripeDesc *descs, int64_t *r_dev, int64_t *P, int64_t *Q, int32_t *map,
-                         PanelScratch gs, int32_t *fallbacks, uint64_t *ptab)
+                         PanelScratch gs, int32_t *fallbacks, uint64_t *ptab, const int32_t *prev_map,
+                         const uint64_t *prev_S, int64_t ldS)
 {
-    panel_kernel<<<1, PANEL_THREADS, 0, st>>>(A, m, ld, npiv, s, descs, r_dev, P, Q, map, gs,
-                                              fallbacks, ptab);
-    return cudaGetLastError();
+    return launch_kernel(panel_kernel, dim3(1), dim3(PANEL_THREADS), 0, st, (const uint64_t *)A, m, ld, npiv, s, descs,
+                         r_dev, P, Q, map, gs, fallbacks, ptab, prev_map, prev_S, ldS);
 }
 
 // ----------------------------------------------------------------------------
@@ -220,8 +228,10 @@ constexpr int PREP_FIRST_ROW_BLOCK = PREP_STAGE_BLOCKS;
 __global__ void __launch_bounds__(PREP_THREADS)
 prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *descs,
             const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *IDX, int32_t *err,
-            const uint64_t *__restrict__ ptab)
+            const uint64_t *__restrict__ ptab, int64_t nw)
 {
+    pdl_wait();
+    pdl_trigger();
     StripeDesc *d = descs + s;
     const int rbar = d->rbar;
     if (rbar == 0) return;
@@ -229,12 +239,25 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
     const int64_t cw = d->c >> 6;
     const int nS = d->nS;
     const int maxpos = d->maxpos;
-    __shared__ uint64_t sE[KS], sLinv[KS];
+    __shared__ uint64_t sE[KS], sLinv[KS], sG[KS];
     for (int i = threadIdx.x; i < rbar; i += blockDim.x) {
         sE[i] = d->E11[i];
         sLinv[i] = d->Linv[i];
+        // word nw of the raw pivot rows (their sources, which no CTA writes here)
+        if (nw >= 0) sG[i] = A[d->S_src[i] * ld + nw];
     }
     __syncthreads();
+    // the stripe's update of word nw for a row with table index ix: the raw
+    // pivot rows selected by ix (the same sum the update kernel looks up)
+    auto next_word = [&](uint64_t ix) -> uint64_t {
+        uint64_t x = 0;
+        while (ix) {
+            const int q = __ffsll((long long)ix) - 1;
+            ix &= ix - 1;
+            x ^= sG[q];
+        }
+        return x;
+    };
 
     if (blockIdx.x < PREP_STAGE_BLOCKS) {
         // staged rows: copy the whole source row, then fix its L region
@@ -267,6 +290,7 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
                     es = 0;
                 }
                 write_lregion(dst, r, cw, rbar, v, es);
+                if (nw >= 0) dst[nw] ^= next_word(ix);
                 IDX[pos] = ix;
             }
             __syncthreads();
@@ -298,6 +322,7 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
         }
         if (g != sw && err) atomicExch(err, 1);
         write_lregion(row, r, cw, rbar, v, 0ull);
+        if (nw >= 0) row[nw] ^= next_word(ix);
         IDX[i] = ix;
     }
 }
@@ -306,14 +331,13 @@ cudaError_t setup_prep_kernel() { return cudaSuccess; }
 
 cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
                         StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
-                        uint64_t *IDX, int32_t *err, const uint64_t *ptab, int num_sms)
+                        uint64_t *IDX, int32_t *err, const uint64_t *ptab, int num_sms, int64_t next_word)
 {
     int64_t blocks = (m + PREP_THREADS - 1) / PREP_THREADS;
     if (blocks < 1) blocks = 1;
     if (blocks > 4 * num_sms) blocks = 4 * num_sms;
-    prep_kernel<<<(int)(blocks + PREP_FIRST_ROW_BLOCK), PREP_THREADS, 0, st>>>(
-        A, m, ld, W, s, descs, map, S, ldS, IDX, err, ptab);
-    return cudaGetLastError();
+    return launch_kernel(prep_kernel, dim3((int)(blocks + PREP_FIRST_ROW_BLOCK)), dim3(PREP_THREADS), 0, st, A, m, ld,
+                         W, s, descs, map, S, ldS, IDX, err, ptab, next_word);
 }
 
 }  // namespace gf2

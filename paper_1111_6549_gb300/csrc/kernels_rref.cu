@@ -20,6 +20,8 @@ namespace gf2 {
 
 __global__ void rref_lclear_kernel(uint64_t *A, int64_t m, int64_t W, int64_t ld, const int64_t *r_dev)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t r = *r_dev;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -42,8 +44,7 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
     int64_t blocks = (m * 32 + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 8 * num_sms) blocks = 8 * num_sms;
-    rref_lclear_kernel<<<(int)blocks, 256, 0, st>>>(A, m, W, ld, r_dev);
-    return cudaGetLastError();
+    return launch_kernel(rref_lclear_kernel, dim3((int)blocks), dim3(256), 0, st, A, m, W, ld, r_dev);
 }
 
 constexpr int RPREP_THREADS = 256;
@@ -52,6 +53,8 @@ __global__ void __launch_bounds__(RPREP_THREADS)
 rref_prep_kernel(uint64_t *A, int64_t ld, int64_t W, int s, const StripeDesc *descs, uint64_t *IDX,
                  int nbr)
 {
+    pdl_wait();
+    pdl_trigger();
     const StripeDesc *d = descs + s;
     const int rbar = d->rbar;
     if (rbar == 0) return;
@@ -97,16 +100,20 @@ cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W
     int64_t nidx = (m + RPREP_THREADS - 1) / RPREP_THREADS;
     if (nidx > 2 * num_sms) nidx = 2 * num_sms;
     if (nidx < 1) nidx = 1;
-    rref_prep_kernel<<<(int)(nbr + nidx), RPREP_THREADS, 0, st>>>(A, ld, W, s, descs, IDX, (int)nbr);
-    return cudaGetLastError();
+    return launch_kernel(rref_prep_kernel, dim3((int)(nbr + nidx)), dim3(RPREP_THREADS), 0, st, A, ld, W, s, descs, IDX,
+                         (int)nbr);
 }
 
-__global__ void copy_rank_kernel(const int64_t *r_dev, int64_t *rank_dev) { *rank_dev = *r_dev; }
+__global__ void copy_rank_kernel(const int64_t *r_dev, int64_t *rank_dev)
+{
+    pdl_wait();
+    pdl_trigger();
+    *rank_dev = *r_dev;
+}
 
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev)
 {
-    copy_rank_kernel<<<1, 1, 0, st>>>(r_dev, rank_dev);
-    return cudaGetLastError();
+    return launch_kernel(copy_rank_kernel, dim3(1), dim3(1), 0, st, r_dev, rank_dev);
 }
 
 // ---- solve: consistency of the transformed right-hand side, then X

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_update_kernel(UpdArgs a)
         r = d->r;
         row_lo = r;
         row_hi = a.m;
-        w_lo = (d->c >> 6) + 1;
+        w_lo = (d->c >> 6) + (a.first_off > 0 ? a.first_off : 1);
         maxpos = d->maxpos;
         nS = d->nS;
         if (tid < KS) sGen[tid] = (tid < rbar) ? a.S + tid * a.ldS : nullptr;

@@ -35,6 +35,8 @@ namespace gf2 {
 template <bool VEC>
 __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) uint64_t T[];
     __shared__ const uint64_t *sGen[KS];
 
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
         r = d->r;
         row_lo = r;
         row_hi = a.m;
-        w_lo = (d->c >> 6) + 1;
+        w_lo = (d->c >> 6) + (a.first_off > 0 ? a.first_off : 1);
         maxpos = d->maxpos;
         nS = d->nS;
         if (threadIdx.x < KS)
@@ -231,6 +233,8 @@ struct RowBatch {
 template <bool WIDE>
 __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) uint64_t T[];
     __shared__ const uint64_t *sGen[KS];
 
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
         r = d->r;
         row_lo = r;
         row_hi = a.m;
-        w_lo = (d->c >> 6) + 1;
+        w_lo = (d->c >> 6) + (a.first_off > 0 ? a.first_off : 1);
         maxpos = d->maxpos;
         nS = d->nS;
         if (threadIdx.x < KS)
@@ -299,7 +303,16 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     // unit 0 holds the first word w_lo either way.
     constexpr int TWK = WIDE ? WT : TW;              // words per tile
     const int64_t a0 = w_lo / TWK, a1 = (W + TWK - 1) / TWK;
-    const int64_t NT = a1 - a0;
+    // an optional skipped word range [skip_lo, skip_hi) (known zero in every
+    // row involved): whole tiles inside it are left out, so tile index t maps
+    // to tile a0 + t below the gap and b0 + (t - n1) after it
+    int64_t n1 = a1 - a0, b0 = a1;
+    if (a.skip_hi > a.skip_lo && a.skip_lo > w_lo && a.skip_hi < W) {
+        const int64_t e1 = (a.skip_lo + TWK - 1) / TWK, bb = a.skip_hi / TWK;
+        if (bb > e1) { n1 = e1 - a0; b0 = bb; }
+    }
+    const int64_t NT = n1 + (a1 - b0);
+    auto phys = [&](int64_t t) -> int64_t { return t < n1 ? a0 + t : b0 + (t - n1); };
     const int64_t NU = WIDE ? NT : (NT + 1) / 2;
     const int64_t tp_lo = min(a.tp_lo, NU);
     const int64_t tp_hi = (a.tp_hi < 0) ? NU : min(a.tp_hi, NU);
@@ -311,9 +324,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     const int64_t u_beg = U * pj / npairs;
     const int64_t u_end = U * (pj + 1) / npairs;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.bytes) {
-        const int64_t wl = max(w_lo, (a0 + (WIDE ? 1 : 2) * tp_lo) * TWK);
-        const int64_t wh = min(W, (a0 + (WIDE ? 1 : 2) * tp_hi) * TWK);
-        atomicAdd(a.bytes, (unsigned long long)(R * (wh - wl) * 16));
+        int64_t words = 0;                           // words of the tiles [units tp_lo, tp_hi)
+        for (int64_t t = (WIDE ? 1 : 2) * tp_lo; t < min(NT, (WIDE ? 1 : 2) * tp_hi); ++t)
+            words += min(W, (phys(t) + 1) * TWK) - max(w_lo, phys(t) * TWK);
+        atomicAdd(a.bytes, (unsigned long long)(R * words * 16));
     }
 
     constexpr int LANES = TWK / 2;                  // threads per row: 16 bytes each
@@ -331,7 +345,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
         u += nrows;
         const int64_t tile = WIDE ? tp_lo + tq : 2 * (tp_lo + tq) + half;
         if (tile >= NT) continue;
-        const int64_t wbase = (a0 + tile) * TWK;
+        const int64_t wbase = phys(tile) * TWK;
         __syncthreads();
         if (WIDE) build_wide_tables(T, sGen, wbase, W);
         else build_tables(T, sGen, wbase, W);
@@ -433,6 +447,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
 // and arguments as the table kernels (PLE, RREF, MUL).
 __global__ void __launch_bounds__(256) naive_update_kernel(UpdArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ const uint64_t *sGen[KS];
     int64_t row_lo, row_hi, w_lo, r = 0;
     int maxpos = -1, nS = 0;
@@ -444,7 +460,7 @@ __global__ void __launch_bounds__(256) naive_update_kernel(UpdArgs a)
         r = d->r;
         row_lo = r;
         row_hi = a.m;
-        w_lo = (d->c >> 6) + 1;
+        w_lo = (d->c >> 6) + (a.first_off > 0 ? a.first_off : 1);
         maxpos = d->maxpos;
         nS = d->nS;
         if (threadIdx.x < KS) sGen[threadIdx.x] = (threadIdx.x < rbar) ? a.S + threadIdx.x * a.ldS : nullptr;
@@ -529,8 +545,7 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
                      ((a.mode != UPD_PLE && a.mode != UPD_M4RI) || (a.ldS % 2 == 0 && (uintptr_t)a.S % 16 == 0));
     int grid = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
     if (a.naive && a.mode != UPD_M4RI) {
-        naive_update_kernel<<<8 * num_sms, 256, 0, st>>>(a);
-        return cudaGetLastError();
+        return launch_kernel(naive_update_kernel, dim3(8 * num_sms), dim3(256), 0, st, a);
     }
     if (vec) {
         grid &= ~1;
@@ -539,12 +554,13 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
             return launch_update_tma(st, a, grid);
         if (a.wide) {
             int gw = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
-            update_pipe_kernel<true><<<gw, UPD_THREADS, WIDE_TAB_WORDS * sizeof(uint64_t), st>>>(a);
+            return launch_kernel(update_pipe_kernel<true>, dim3(gw), dim3(UPD_THREADS),
+                                 WIDE_TAB_WORDS * sizeof(uint64_t), st, a);
         } else {
-            update_pipe_kernel<false><<<grid, UPD_THREADS, smem, st>>>(a);
+            return launch_kernel(update_pipe_kernel<false>, dim3(grid), dim3(UPD_THREADS), smem, st, a);
         }
     } else {
-        update_kernel<false><<<grid, UPD_THREADS, smem, st>>>(a);
+        return launch_kernel(update_kernel<false>, dim3(grid), dim3(UPD_THREADS), smem, st, a);
     }
     return cudaGetLastError();
 }

@@ -60,7 +60,7 @@ update_tma_kernel(UpdArgs a, const __grid_constant__ TensorMap2D tm)
         r = d->r;
         row_lo = r;
         row_hi = a.m;
-        w_lo = (d->c >> 6) + 1;
+        w_lo = (d->c >> 6) + (a.first_off > 0 ? a.first_off : 1);
         maxpos = d->maxpos;
         nS = d->nS;
         if (threadIdx.x < KS)

@@ -26,9 +26,31 @@ struct PanelShared {
     int cnt, nz;
     int wcnt[32];
     int32_t zpos[KS], zsrc[KS];
-    // transposed window path (panel_window_t): rows of L11^-1 and U11^-1
-    uint64_t Linv[KS], Minv[KS];
 };
+
+// Where a row's stripe word lives while the previous stripe's trailing
+// update may still be running (the look-ahead of the block-iterative PLE):
+// rows that the previous stripe's swaps moved are read from its staged
+// copies, which already hold their updated word of this stripe; every other
+// row is read in place.  map == nullptr: every row in place.
+struct PrevStage {
+    const int32_t *map;   // the previous stripe's row map (position -> stripe * 256 + staged slot)
+    const uint64_t *S;    // its staged rows
+    int64_t ldS;
+    int64_t r;            // its first row position
+    int maxpos;           // its largest staged position offset
+    int stripe;           // its index
+};
+
+__device__ __forceinline__ uint64_t stripe_word(const uint64_t *__restrict__ A, int64_t ld, int64_t cw, int64_t p,
+                                                const PrevStage &ps)
+{
+    if (ps.map && p >= ps.r && p - ps.r <= ps.maxpos) {
+        const int mv = ps.map[p];
+        if (mv >= 0 && (mv >> 8) == ps.stripe) return ps.S[(int64_t)(mv & 255) * ps.ldS + cw];
+    }
+    return A[p * ld + cw];
+}
 
 // One of four registers by a warp-uniform index (no local-memory array).
 template <typename T>
@@ -47,7 +69,8 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int b)
 // may lie outside the window; otherwise sh.rbar, E, L, t, j and the
 // staged-row list.
 __device__ __forceinline__ void panel_window(const uint64_t *__restrict__ A, int64_t r, int64_t ld,
-                                             int64_t cw, int64_t rows, int keff, PanelShared &sh)
+                                             int64_t cw, int64_t rows, int keff, PanelShared &sh,
+                                             const PrevStage ps = PrevStage{nullptr, nullptr, 0, 0, -1, -1})
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -57,7 +80,7 @@ __device__ __forceinline__ void panel_window(const uint64_t *__restrict__ A, int
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         const int sl = b * 32 + lane;
-        R[b] = (sl < Wn) ? A[(r + sl) * ld + cw] : 0ull;
+        R[b] = (sl < Wn) ? stripe_word(A, ld, cw, r + sl, ps) : 0ull;
         Lc[b] = 0ull;
         org[b] = sl;
     }
@@ -153,7 +176,8 @@ __device__ __forceinline__ void panel_window(const uint64_t *__restrict__ A, int
 // that are zero in every remaining row are skipped outright.
 __device__ __forceinline__ void panel_block(const uint64_t *__restrict__ A, int64_t r, int64_t ld,
                                             int64_t cw, int64_t rows, int keff, PanelScratch gs,
-                                            PanelShared &sh, int32_t *fallbacks)
+                                            PanelShared &sh, int32_t *fallbacks,
+                                            const PrevStage ps = PrevStage{nullptr, nullptr, 0, 0, -1, -1})
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = blockDim.x;
@@ -172,7 +196,7 @@ __device__ __forceinline__ void panel_block(const uint64_t *__restrict__ A, int6
     const int64_t c0 = min(rows, (int64_t)tid * chunk), c1 = min(rows, c0 + chunk);
     int mine = 0;
     for (int64_t sl = c0; sl < c1; ++sl) {
-        const uint64_t v = A[(r + sl) * ld + cw];
+        const uint64_t v = stripe_word(A, ld, cw, r + sl, ps);
         orv |= v;
         mine += (v != 0ull);
     }
@@ -188,7 +212,7 @@ __device__ __forceinline__ void panel_block(const uint64_t *__restrict__ A, int6
     for (int w2 = 0; w2 < warp; ++w2) off += sh.wcnt[w2];
     if (tid == nthr - 1) sh.cnt = off + mine;
     for (int64_t sl = c0; sl < c1; ++sl) {
-        const uint64_t v = A[(r + sl) * ld + cw];
+        const uint64_t v = stripe_word(A, ld, cw, r + sl, ps);
         if (v != 0ull) {
             gs.val[off] = v;
             gs.lb[off] = 0;
@@ -321,198 +345,96 @@ __device__ __forceinline__ void warp_lower_inverse(const uint64_t *Lrows, int rb
     }
 }
 
-// Column `lane` of a 32 x 32 bit block: lane i passes row i (bit j = entry
-// (i, j)), lane l gets bit i = entry (i, l).  Five butterfly exchanges of
-// halving sub-blocks.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
-{
-    const int lane = threadIdx.x & 31;
-    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int d = 16 >> k;
-        const uint32_t m = masks[k];
-        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, d);
-        x = (lane & d) ? (((y >> d) & m) | (x & ~m)) : ((x & m) | ((y & m) << d));
-    }
-    return x;
-}
+// Fast path over four warps (threads 0..127 of the block, every one of them
+// must call it): the same search as panel_window, with window slot i held by
+// thread i (its stripe word, its L coefficients, the slot its content came
+// from).  Per column: one ballot per warp, the four ballots and then the
+// pivot row (and the row it swaps with) exchanged through shared memory
+// between two 128-thread barriers, and one conditional XOR per thread.  The
+// exchange buffers alternate between two halves by step parity, so a step's
+// writes never meet the previous step's reads.  Sets sh.fail exactly when
+// panel_window would.
+__device__ __forceinline__ void panel_bar128() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
 
-// 64 x 64 bit matrix held by columns (lane l: columns l and l + 32, bit p =
-// row p) -> by rows (lane l: rows l and l + 32, bit q = column q).
-__device__ __forceinline__ void warp_transpose64(uint64_t c0, uint64_t c1, uint64_t &r0, uint64_t &r1)
+__device__ __forceinline__ void panel_window4(const uint64_t *__restrict__ A, int64_t r, int64_t ld,
+                                              int64_t cw, int64_t rows, int keff, PanelShared &sh,
+                                              const PrevStage &ps)
 {
-    const uint32_t a = warp_transpose32((uint32_t)c0), b = warp_transpose32((uint32_t)c1);
-    const uint32_t c = warp_transpose32((uint32_t)(c0 >> 32)), e = warp_transpose32((uint32_t)(c1 >> 32));
-    r0 = ((uint64_t)b << 32) | a;
-    r1 = ((uint64_t)e << 32) | c;
-}
-
-// A set of the 128 window slots: lo = slots 0..63, hi = slots 64..127.
-struct SlotMask {
-    uint64_t lo, hi;
-};
-
-// Exchange slots p (< 64) and t (> p) in m; pt = the mask of both slots.
-__device__ __forceinline__ void slot_swap(SlotMask &m, int p, int t, const SlotMask &pt)
-{
-    const uint64_t bp = (m.lo >> p) & 1ull;
-    const uint64_t bt = t < 64 ? ((m.lo >> t) & 1ull) : ((m.hi >> (t - 64)) & 1ull);
-    const uint64_t sel = 0ull - (bp ^ bt);
-    m.lo ^= pt.lo & sel;
-    m.hi ^= pt.hi & sel;
-}
-
-// Transposed fast path, called by one whole warp: the same search as
-// panel_window (Algorithm 1 on a window of up to 128 rows), with the window
-// held by columns -- lane l owns the slot masks of columns l and l + 32 --
-// so that a pivot step is one broadcast of column j's mask, a find-first-set
-// and a few mask operations per lane.  Besides E, L, t, j and the staged-row
-// list it leaves L11^-1 and U11^-1 in sh.Linv / sh.Minv, taken from masks
-// kept during the elimination:
-//   * L11: pivot q's mask of the slots it eliminated (the rows below it);
-//   * L11^-1: per slot, which earlier pivot rows' raw contents its content
-//     holds beside its own (V); at its selection, pivot p's row is its own raw
-//     row plus V_p, so row p of L11^-1 is e_p + V_p;
-//   * U11^-1: each pivot also clears its column from the earlier pivot rows
-//     (their contents become the fully reduced rows, GaussSubmatrix); the set
-//     it cleared is column q of U11^-1 above the diagonal.
-// The pivot rows' echelon form E (before that reduction) is taken by ballot
-// at each selection.  Sets sh.fail exactly when panel_window would.
-__device__ __forceinline__ void panel_window_t(const uint64_t *__restrict__ A, int64_t r, int64_t ld,
-                                               int64_t cw, int64_t rows, int keff, PanelShared &sh)
-{
-    const int lane = threadIdx.x & 31;
+    __shared__ unsigned sb[2][4];
+    __shared__ uint64_t sv[2][2], sl[2][2];
+    __shared__ int so[2][2];
+    const int slot = threadIdx.x, lane = slot & 31, w = slot >> 5;
     const unsigned FULL = 0xffffffffu;
     const int Wn = (int)min(rows, (int64_t)PANEL_WIN);
-    uint64_t R[4];
-    int org[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int sl = b * 32 + lane;
-        R[b] = (sl < Wn) ? A[(r + sl) * ld + cw] : 0ull;
-        org[b] = sl;
-    }
-    // columns: Mc[h] = slots holding column 32 h + lane
-    SlotMask Mc[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const uint64_t s0 = warp_transpose32((uint32_t)(R[0] >> (32 * h)));
-        const uint64_t s1 = warp_transpose32((uint32_t)(R[1] >> (32 * h)));
-        const uint64_t s2 = warp_transpose32((uint32_t)(R[2] >> (32 * h)));
-        const uint64_t s3 = warp_transpose32((uint32_t)(R[3] >> (32 * h)));
-        Mc[h].lo = s0 | (s1 << 32);
-        Mc[h].hi = s2 | (s3 << 32);
-    }
-    SlotMask LM[2] = {{0, 0}, {0, 0}}, VM[2] = {{0, 0}, {0, 0}};   // pivots lane, lane + 32
-    uint64_t UM[2] = {0, 0}, Er[2] = {0, 0};
-    int p = 0, tmax = -1;
+    uint64_t R = (slot < Wn) ? stripe_word(A, ld, cw, r + slot, ps) : 0ull;
+    uint64_t Lc = 0;
+    int org = slot;
+    int p = 0, tmax = -1, ph = 0;
     bool fail = false;
     for (int j = 0; j < keff && p < Wn; ++j) {
-        const int jh = j >> 5, jl = j & 31;
-        const SlotMask src = jh ? Mc[1] : Mc[0];
-        SlotMask Mj;
-        Mj.lo = __shfl_sync(FULL, src.lo, jl);
-        Mj.hi = __shfl_sync(FULL, src.hi, jl);
-        const uint64_t clo = Mj.lo & (~0ull << p);        // p < 64: slots >= p
-        if (!(clo | Mj.hi)) {
-            if (Wn < rows) { fail = true; break; }       // the pivot may lie outside the window
-            continue;                                    // column j has no pivot
+        const unsigned b = __ballot_sync(FULL, (unsigned)(R >> j) & 1u);
+        if (lane == 0) sb[ph][w] = b;
+        panel_bar128();
+        const uint64_t lo = (((uint64_t)sb[ph][1] << 32) | sb[ph][0]) & ((p < 64) ? (~0ull << p) : 0ull);
+        const uint64_t hi = (((uint64_t)sb[ph][3] << 32) | sb[ph][2]) & ((p < 64) ? ~0ull : (~0ull << (p - 64)));
+        int t;
+        if (lo) t = __ffsll((long long)lo) - 1;
+        else if (hi) t = 64 + __ffsll((long long)hi) - 1;
+        else {
+            if (Wn < rows) { fail = true; break; }   // the pivot may lie outside the window
+            ph ^= 1;
+            continue;                                // column j has no pivot
         }
-        const int t = clo ? __ffsll((long long)clo) - 1 : 64 + __ffsll((long long)Mj.hi) - 1;
+        // the pivot row (slot t) and the row it exchanges with (slot p)
+        if (slot == t) { sv[ph][0] = R; sl[ph][0] = Lc; so[ph][0] = org; }
+        if (slot == p) { sv[ph][1] = R; sl[ph][1] = Lc; so[ph][1] = org; }
+        panel_bar128();
+        const uint64_t prow = sv[ph][0];
         if (t != p) {
-            SlotMask pt;
-            pt.lo = (1ull << p) | (t < 64 ? (1ull << t) : 0ull);
-            pt.hi = t < 64 ? 0ull : (1ull << (t - 64));
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                slot_swap(Mc[h], p, t, pt);
-                slot_swap(LM[h], p, t, pt);
-                slot_swap(VM[h], p, t, pt);
-            }
-            slot_swap(Mj, p, t, pt);
-            const int op = __shfl_sync(FULL, pick4(org, p >> 5), p & 31);
-            const int ot = __shfl_sync(FULL, pick4(org, t >> 5), t & 31);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                if (32 * b + lane == p) org[b] = ot;
-                if (32 * b + lane == t) org[b] = op;
-            }
+            if (slot == p) { R = prow; Lc = sl[ph][0]; org = so[ph][0]; }
+            else if (slot == t) { R = sv[ph][1]; Lc = sl[ph][1]; org = so[ph][1]; }
         }
-        // the pivot row (now slot p): its echelon word, by ballot
-        const unsigned elo = __ballot_sync(FULL, (unsigned)(Mc[0].lo >> p) & 1u);
-        const unsigned ehi = __ballot_sync(FULL, (unsigned)(Mc[1].lo >> p) & 1u);
-        SlotMask below;
-        below.lo = Mj.lo & ((p == 63) ? 0ull : (~0ull << (p + 1)));
-        below.hi = Mj.hi;
-        const uint64_t above = Mj.lo & ((1ull << p) - 1ull);
-        // clear column j from every other slot holding it: the columns the
-        // pivot row holds take (below + above); V of the rows below takes
-        // V_p + e_p
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint64_t sc = 0ull - ((Mc[h].lo >> p) & 1ull);
-            Mc[h].lo ^= (below.lo | above) & sc;
-            Mc[h].hi ^= below.hi & sc;
-            const uint64_t sv = 0ull - ((VM[h].lo >> p) & 1ull);
-            VM[h].lo ^= below.lo & sv;
-            VM[h].hi ^= below.hi & sv;
+        // eliminate column j from the slots after p holding it (slot t now
+        // holds the old row p, zero in column j)
+        if (slot > p && ((R >> j) & 1ull)) {
+            R ^= prow;
+            Lc |= 1ull << p;
         }
-        if (lane == (p & 31)) {
-            const int h = p >> 5;
-            const uint64_t e = ((uint64_t)ehi << 32) | elo;
-            if (h == 0) { VM[0].lo ^= below.lo; VM[0].hi ^= below.hi; LM[0] = below; UM[0] = above; Er[0] = e; }
-            else        { VM[1].lo ^= below.lo; VM[1].hi ^= below.hi; LM[1] = below; UM[1] = above; Er[1] = e; }
-        }
-        if (lane == 0) {
+        if (slot == 0) {
             sh.t[p] = t;
             sh.j[p] = (uint8_t)j;
         }
         tmax = max(tmax, t);
         ++p;
+        ph ^= 1;
     }
     if (!fail) {
-        // rows of L11 (bit q < p: pivot q cleared row p), of L11^-1 (e_p + V_p)
-        // and of U11^-1 (e_p + the later pivots that cleared their column
-        // from row p), by transposing the per-pivot masks
-        uint64_t l0, l1, v0, v1, u0, u1;
-        warp_transpose64(LM[0].lo, LM[1].lo, l0, l1);
-        warp_transpose64(VM[0].lo, VM[1].lo, v0, v1);
-        warp_transpose64(UM[0] | (1ull << lane), UM[1] | (1ull << (lane + 32)), u0, u1);
-        const uint64_t below_diag0 = (lane == 0) ? 0ull : (~0ull >> (64 - lane));
-        const uint64_t below_diag1 = ~0ull >> (32 - lane);
-        if (lane < p) {
-            sh.E[lane] = Er[0];
-            sh.L[lane] = l0 & below_diag0;
-            sh.Linv[lane] = ((v0 & below_diag0) | (1ull << lane));
-            sh.Minv[lane] = u0 & ~below_diag0 & ((p == 64) ? ~0ull : ((1ull << p) - 1ull));
+        // slots 0 .. p-1 hold the pivot rows (echelon); their L bits are below their index
+        if (slot < p) {
+            sh.E[slot] = R;
+            sh.L[slot] = Lc & ((slot == 0) ? 0ull : (~0ull >> (64 - slot)));
         }
-        if (lane + 32 < p) {
-            sh.E[lane + 32] = Er[1];
-            sh.L[lane + 32] = l1 & below_diag1;
-            sh.Linv[lane + 32] = ((v1 & below_diag1) | (1ull << (lane + 32)));
-            sh.Minv[lane + 32] = u1 & ~below_diag1 & ((p == 64) ? ~0ull : ((1ull << p) - 1ull));
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) sh.perm[32 * b + lane] = org[b];
-        __syncwarp();
-        // staged rows: pivot rows first, then rows displaced into [p, tmax]
-        for (int k = lane; k < p; k += 32) { sh.Soff[k] = k; sh.Ssrc[k] = r + sh.perm[k]; }
-        int base = p;
-        for (int b0 = p; b0 <= tmax; b0 += 32) {
-            const int sl = b0 + lane;
-            const bool mv = sl <= tmax && sh.perm[sl] != sl;
-            const unsigned bm = __ballot_sync(FULL, mv);
-            if (mv) {
-                const int k = base + __popc(bm & ((1u << lane) - 1u));
-                sh.Soff[k] = sl;
-                sh.Ssrc[k] = r + sh.perm[sl];
+        sh.perm[slot] = org;
+        panel_bar128();
+        if (w == 0) {
+            // staged rows: pivot rows first, then rows displaced into [p, tmax]
+            for (int k = lane; k < p; k += 32) { sh.Soff[k] = k; sh.Ssrc[k] = r + sh.perm[k]; }
+            int base = p;
+            for (int b0 = p; b0 <= tmax; b0 += 32) {
+                const int sl2 = b0 + lane;
+                const bool mv = sl2 <= tmax && sh.perm[sl2] != sl2;
+                const unsigned bm = __ballot_sync(FULL, mv);
+                if (mv) {
+                    const int k = base + __popc(bm & ((1u << lane) - 1u));
+                    sh.Soff[k] = sl2;
+                    sh.Ssrc[k] = r + sh.perm[sl2];
+                }
+                base += __popc(bm);
             }
-            base += __popc(bm);
+            if (lane == 0) { sh.nS = base; sh.maxpos = max(p - 1, tmax); }
         }
-        if (lane == 0) { sh.nS = base; sh.maxpos = max(p - 1, tmax); }
     }
-    if (lane == 0) { sh.fail = fail ? 1 : 0; sh.rbar = p; }
+    if (slot == 0) { sh.fail = fail ? 1 : 0; sh.rbar = p; }
 }
 
 }  // namespace gf2

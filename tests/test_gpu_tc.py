@@ -183,3 +183,54 @@ def test_naive_update_ple_and_rref(m, n):
     R0 = A.copy()
     oracle.rref(R0, m, n)
     assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+
+
+@pytest.mark.parametrize("m,n,block", [(1000, 1500, 0), (2048, 2048, 512), (3000, 2500, 1024), (700, 900, 128)])
+def test_pdl_launches_ple_rref_mul(m, n, block):
+    """GF2_OPT_PDL: every kernel scheduled while its predecessor on the stream
+    runs and waiting on the device for it -- the same unique results, with the
+    blocked PLE and RREF (TRSM leaves and products) and the look-ahead."""
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    hh.set_option(g.OPT_PDL, 1)
+    if block:
+        hh.set_option(g.OPT_PLE_BLOCK, block)
+        hh.set_option(g.OPT_RREF_BLOCK, block)
+        hh.set_option(g.OPT_MUL_GEMM_MIN_K, 256)
+    A = gi.bernoulli_matrix(m, n, 9 * m + n)
+    dA = to_dev(A)
+    P, Q = vec_dev(m), vec_dev(min(m, n))
+    r = hh.ple(dA, m, n, P, Q)
+    LE = A.copy()
+    r0, P0, Q0 = oracle.ple(LE, m, n)
+    assert r == r0 and np.array_equal(P.cpu().numpy()[:m], P0)
+    assert np.array_equal(Q.cpu().numpy()[:min(m, n)], Q0)
+    assert np.array_equal(to_host(dA, gi.words_for(n)), LE)
+    dR = to_dev(A)
+    assert hh.rref(dR, m, n, Q) == r0
+    R0 = A.copy()
+    oracle.rref(R0, m, n)
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+    B = gi.bernoulli_matrix(n, 300, 3)
+    dC = to_dev(np.zeros((m, gi.words_for(300)), np.uint64))
+    hh.mul(dC, to_dev(A), to_dev(B), m, n, 300)
+    assert np.array_equal(to_host(dC), oracle.mul(A, B, m, n, 300))
+
+
+def test_profiling_timeline():
+    """Profiling level 4 keeps one (kind, start, end) record per launch."""
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    m = n = 1024
+    A = gi.bernoulli_matrix(m, n, 77)
+    dA = to_dev(A)
+    P, Q = vec_dev(m), vec_dev(n)
+    hh.reset_stats()
+    hh.set_profiling(4)
+    hh.ple(dA, m, n, P, Q)
+    tl = hh.timeline()
+    st = hh.stats()
+    assert 0 < len(tl) <= st["kernel_launches"]
+    kinds = {k for k, _, _ in tl}
+    assert {0, 1, 2} <= kinds
+    assert all(0.0 <= t0 <= t1 for _, t0, t1 in tl)
