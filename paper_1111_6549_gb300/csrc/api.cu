@@ -102,7 +102,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int64_t words_for(int64_t n) { return (n + 63) >> 6; }
 
 struct Layout {
-    size_t descs, idx, map, S, G, ptab, gval, glb, gsrc, P, Q, total;
+    size_t descs, idx, idx2, gb, map, S, G, ptab, gval, glb, gsrc, P, Q, total;
     int64_t ldS;
 };
 
@@ -116,6 +116,8 @@ Layout layout_for(int64_t m, int64_t ncols)
     size_t off = 0;
     L.descs = off; off = align256(off + (size_t)ns * sizeof(StripeDesc));
     L.idx = off;   off = align256(off + (size_t)mm * 8);
+    L.idx2 = off;  off = align256(off + (size_t)mm * 8);                // fused RREF: the next pass's index
+    L.gb = off;    off = align256(off + 2 * (size_t)KS * L.ldS * 8);    // fused RREF: reduced pivot rows, by parity
     L.map = off;   off = align256(off + (size_t)mm * 8);   // two halves, by stripe parity
     L.S = off;     off = align256(off + (size_t)SMAX * L.ldS * 8);
     L.G = off;     off = align256(off + (size_t)KS * L.ldS * 8);     // M4RI: reduced pivot rows
@@ -528,6 +530,74 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         a.w_lo = skip_hi;
         return launch_update_counted(h, a);
     };
+    // The passes of stripes [sa, sb) from the last to the first over the rows
+    // [row_lo, r_s).  With the wide table kernel each pass is one launch: the
+    // kernel forms the stripe's reduced pivot rows itself (UpdArgs::
+    // rref_fused), writes them back one pass later and takes the next pass's
+    // index; two small launches bracket the block.  Otherwise rref_prep and
+    // the update per stripe.
+    uint64_t *IDX2 = reinterpret_cast<uint64_t *>(h->ws + L.idx2);
+    uint64_t *GB = reinterpret_cast<uint64_t *>(h->ws + L.gb);
+    auto idx_of = [&](int64_t s) { return (s & 1) ? IDX2 : IDX; };
+    auto gb_of = [&](int64_t s) { return GB + (s & 1) * (int64_t)KS * L.ldS; };
+    UpdArgs fprobe{};
+    fprobe.mode = UPD_RREF;
+    fprobe.A = A;
+    fprobe.ld = ld;
+    const bool fusable = update_vectorised(fprobe) && h->wide_update && !h->tc_update && !h->tma && !h->naive_update;
+    auto passes = [&](int64_t sa, int64_t sb, int64_t row_lo, int64_t skip_lo, int64_t skip_hi) -> int {
+        if (!fusable) {
+            for (int64_t s = sb - 1; s >= sa; --s) {
+                int rc = stripe(s, row_lo, skip_lo, skip_hi);
+                if (rc) return rc;
+            }
+            return GF2_OK;
+        }
+        const bool split = skip_lo < skip_hi;
+        const int64_t Wp = split && skip_hi >= W ? skip_lo : W;
+        const int64_t sk_lo = split && skip_hi < W ? skip_lo : 0, sk_hi = split && skip_hi < W ? skip_hi : 0;
+        {
+            Timed t(h, K_RPREP);
+            CK(launch_rref_aux(h->stream, A, ld, nullptr, nullptr, L.ldS, Wp, sk_lo, sk_hi, descs + (sb - 1),
+                               idx_of(sb - 1), row_lo, h->num_sms));
+        }
+        h->launches += 1;
+        for (int64_t s = sb - 1; s >= sa; --s) {
+            UpdArgs a{};
+            a.tp_lo = 0;
+            a.tp_hi = -1;
+            a.left_copies = 1;
+            a.mode = UPD_RREF;
+            a.A = A;
+            a.ld = ld;
+            a.m = m;
+            a.W = Wp;
+            a.skip_lo = sk_lo;
+            a.skip_hi = sk_hi;
+            a.row_lo = row_lo;
+            a.desc = descs + s;
+            a.stripe = (int)s;
+            a.idx = idx_of(s);
+            a.idx_stride = 1;
+            a.bytes = bytes_dev(h);
+            a.rref_fused = 1;
+            a.gbuf_w = gb_of(s);
+            a.gbuf_r = gb_of(s + 1);
+            a.ldg = L.ldS;
+            a.flush_desc = s + 1 < sb ? descs + (s + 1) : nullptr;
+            a.snap_desc = s > sa ? descs + (s - 1) : nullptr;
+            a.idx_next = idx_of(s - 1);
+            int rc = launch_update_counted(h, a);
+            if (rc) return rc;
+        }
+        {
+            Timed t(h, K_RPREP);
+            CK(launch_rref_aux(h->stream, A, ld, descs + sa, gb_of(sa), L.ldS, Wp, sk_lo, sk_hi, nullptr, nullptr,
+                               row_lo, h->num_sms));
+        }
+        h->launches += 1;
+        return GF2_OK;
+    };
     // Blocked form (recursive halving down to blocks of rref_base stripes).
     // Invariant of a call on the stripes [a, b): their pivot rows [r_a, r_b)
     // are already zero on every pivot column of the stripes >= b.  The call
@@ -567,13 +637,7 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
             const int64_t ra = rs[(size_t)a], rb = rs[(size_t)b];
             if (rb == ra) return GF2_OK;                     // no pivot rows: nothing to reduce
             const int64_t sk = skip_end(b);
-            if (b - a <= base) {
-                for (int64_t s = b - 1; s >= a; --s) {
-                    int rc = stripe(s, ra, b < ns ? b : W, sk);
-                    if (rc) return rc;
-                }
-                return GF2_OK;
-            }
+            if (b - a <= base) return passes(a, b, ra, b < ns ? b : W, sk);
             const int64_t mid = (a + b + 1) / 2;
             int rc = rec(mid, b);
             if (rc) return rc;
@@ -603,11 +667,7 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         };
         return rec(0, ns);
     }
-    for (int64_t s = ns - 1; s >= 0; --s) {
-        int rc = stripe(s, 0, W, W);
-        if (rc) return rc;
-    }
-    return GF2_OK;
+    return passes(0, ns, 0, W, W);
 }
 
 // Enqueue M4RI (Algorithm 8): the RREF in one sweep over the stripes.  Per

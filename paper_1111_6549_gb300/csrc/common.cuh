@@ -148,6 +148,20 @@ struct UpdArgs {
     int wide;                  // aligned rows: 128-byte tiles with nine tables (else paired 64-byte tiles)
     int naive;                 // plain baseline: generator rows added one by one, no tables
     int first_off;             // PLE: first updated word = stripe word + first_off (0: 1)
+    // RREF passes with the block reduction fused in (wide table kernel only):
+    // each CTA forms the stripe's reduced pivot rows G = U11^-1 rows for its
+    // tiles in shared memory and writes them to gbuf_w (row t of the stripe
+    // at gbuf_w + t * ldg); the pass also writes the previous pass's G from
+    // gbuf_r back into that stripe's pivot rows (flush_desc, may be null)
+    // and takes the next pass's table index -- the stripe word of rows
+    // [row_lo, r) of snap_desc -- into idx_next (snap_desc may be null).
+    int rref_fused;
+    uint64_t *gbuf_w;
+    const uint64_t *gbuf_r;
+    int64_t ldg;
+    const StripeDesc *flush_desc;
+    const StripeDesc *snap_desc;
+    uint64_t *idx_next;
     int64_t skip_lo, skip_hi;  // words [skip_lo, skip_hi) may be left out (zero in every row
                                // involved); only the pipelined table kernel uses it
 };
@@ -193,6 +207,13 @@ cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t 
                                const int64_t *r_dev, int num_sms);
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, uint64_t *IDX, int64_t m, int num_sms);
+// The fused RREF passes' bookends: flush_desc (may be null): the stripe's
+// reduced pivot rows from gbuf into A over the words [c >> 6, W) except
+// [skip_lo, skip_hi); snap_desc (may be null): the stripe word of rows
+// [row_lo, r) into idx.
+cudaError_t launch_rref_aux(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *flush_desc,
+                            const uint64_t *gbuf, int64_t ldg, int64_t W, int64_t skip_lo, int64_t skip_hi,
+                            const StripeDesc *snap_desc, uint64_t *idx, int64_t row_lo, int num_sms);
 cudaError_t launch_copy_rank(cudaStream_t st, const int64_t *r_dev, int64_t *rank_dev);
 // GF(2) product through the own FP4 tcgen05 GEMM (kernels_gemm_f4.cu): A4
 // a_rows >= max(m, 256) and B4t b_rows >= max(n, 192) rows of kp / 2 bytes

@@ -104,6 +104,41 @@ cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W
                          (int)nbr);
 }
 
+// Bookends of a block of fused RREF passes (see UpdArgs::rref_fused): the
+// first pass's table index (the stripe word of the rows above it) and, after
+// the last pass, its reduced pivot rows from the buffer into A.
+__global__ void rref_aux_kernel(uint64_t *A, int64_t ld, const StripeDesc *flush_desc, const uint64_t *gbuf,
+                                int64_t ldg, int64_t W, int64_t skip_lo, int64_t skip_hi,
+                                const StripeDesc *snap_desc, uint64_t *idx, int64_t row_lo)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    if (flush_desc) {
+        const int rbar = flush_desc->rbar;
+        const int64_t c0 = flush_desc->c >> 6;
+        const int64_t nw = W - c0;
+        if (rbar > 0 && nw > 0)
+            for (int64_t e = gt; e < rbar * nw; e += gs) {
+                const int64_t t = e / nw, word = c0 + (e - t * nw);
+                if (word >= skip_lo && word < skip_hi) continue;
+                A[(flush_desc->r + t) * ld + word] = gbuf[t * ldg + word];
+            }
+    }
+    if (snap_desc) {
+        const int64_t cw = snap_desc->c >> 6;
+        for (int64_t i = row_lo + gt; i < snap_desc->r; i += gs) idx[i] = A[i * ld + cw];
+    }
+}
+
+cudaError_t launch_rref_aux(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *flush_desc,
+                            const uint64_t *gbuf, int64_t ldg, int64_t W, int64_t skip_lo, int64_t skip_hi,
+                            const StripeDesc *snap_desc, uint64_t *idx, int64_t row_lo, int num_sms)
+{
+    return launch_kernel(rref_aux_kernel, dim3(2 * num_sms), dim3(256), 0, st, A, ld, flush_desc, gbuf, ldg, W,
+                         skip_lo, skip_hi, snap_desc, idx, row_lo);
+}
+
 __global__ void copy_rank_kernel(const int64_t *r_dev, int64_t *rank_dev)
 {
     pdl_wait();

@@ -75,4 +75,30 @@ __device__ __forceinline__ void build_wide_tables(uint64_t *T, const uint64_t *c
     }
 }
 
+// As build_wide_tables, with the 64 generator rows of the tile in shared
+// memory (G[row * WT + word]).
+__device__ __forceinline__ void build_wide_tables_smem(uint64_t *T, const uint64_t *G)
+{
+    for (int item = threadIdx.x; item < 40 * WT; item += blockDim.x) {
+        const int w = item % WT, seg = item / WT;
+        const int t = seg < 32 ? seg >> 2 : 8;
+        const int q = seg < 32 ? seg & 3 : seg - 32;
+        const int nb = t < 8 ? 7 : 8;
+        uint64_t g[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) g[b] = b < nb ? G[(7 * t + b) * WT + w] : 0ull;
+        uint64_t val = ((q & 1) ? g[5] : 0ull) ^ ((q & 2) ? g[6] : 0ull) ^ ((q & 4) ? g[7] : 0ull);
+        uint64_t *Tt = T + (int64_t)(128 * t + 32 * q) * WT + w;
+        int x = 0;
+        Tt[0] = val;
+#pragma unroll
+        for (int i = 1; i < 32; ++i) {
+            const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4;
+            x ^= 1 << b;
+            val ^= g[b];
+            Tt[x * WT] = val;
+        }
+    }
+}
+
 }  // namespace gf2
