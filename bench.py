@@ -45,6 +45,15 @@ def work_bits(m: int, n: int, r: int) -> float:
     return m * n * r - (m + n) * r * r / 2.0 + r ** 3 / 3.0
 
 
+def bf16_peak():
+    """Measured dense bf16 TFLOP/s (burst) of this machine's GB300, for the GEMM's roofline."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -77,6 +86,27 @@ def update_kernel_traffic():
         if mh and mt and mh.group(1) == digest:
             return float(mt.group(1)), os.path.relpath(path, ROOT)
     return None, None
+
+
+def batched_alu_counters():
+    """ALU-pipe instructions of one batched_ple_kernel launch on the 4096-matrix
+    batch and the pipe's peak per cycle, from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    h = hashlib.sha256()
+    for name in ("kernels_batched.cu", "panel_dev.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1111_6549_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "batched_ple_kernel.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    mi = re.search(r"alu_inst_per_launch:\s*([0-9.eE+]+)", text)
+    mp = re.search(r"alu_peak_inst_per_cycle:\s*([0-9.eE+]+)", text)
+    if not (mh and mi and mp) or mh.group(1) != digest:
+        return None
+    return float(mi.group(1)), float(mp.group(1)), os.path.relpath(path, ROOT)
 
 
 class ClockSampler:
@@ -324,7 +354,27 @@ def bench_batched(h, torch, dev, stream, reps: int = 5):
     torch.cuda.synchronize()
     t_plain = a.elapsed_time(b)
     hbm, _ = peaks()
+    # roofline against the ALU pipe (the batched kernel keeps every matrix in
+    # shared memory and L2; its bound is integer logic, not HBM)
+    alu = batched_alu_counters()
+    clk_mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            clk_mhz = float(json.load(fh).get("sm_max_mhz", clk_mhz))
+    except Exception:
+        pass
+    broof = None
+    if alu:
+        inst, peak_pc, src = alu
+        ach = inst / (t_default / 1e3)          # the counters were taken in the default configuration
+        pk = peak_pc * clk_mhz * 1e6
+        broof = {"kernel": "batched_ple_kernel", "bound": "alu", "achieved": ach, "peak": pk,
+                 "unit": "ALU-pipe warp instructions/s", "frac": ach / pk,
+                 "source": f"{src}: ALU-pipe instructions of one launch on this batch and the pipe's peak per "
+                           f"cycle (ncu, default configuration), over this run's default-configuration time; "
+                           f"peak at {clk_mhz:.0f} MHz"}
     return {"workload": "4096 matrices, m,n ~ U{64..1024}, Bernoulli(1/2), 25% with 10% rows zeroed",
+            "roofline": broof,
             "ms": t, "mats_per_s": len(specs) / (t / 1e3), "gbitops": wsum / (t / 1e3) / 1e9,
             "hbm_gbs_algorithmic": nbytes / (t / 1e3) / 1e9,
             "hbm_frac": nbytes / (t / 1e3) / 1e9 / hbm,
@@ -646,26 +696,34 @@ def run_ours(args):
     upd_per_launch_bytes = st["update_bytes"] / max(st["update_timed_launches"], 1)
     ratio, ratio_src = update_kernel_traffic()
     traffic = ratio * upd_per_launch_bytes if ratio is not None else None
-    roofline = {"kernel": "update_pipe_kernel (tabulated trailing update: PLE stripes, TRSM and RREF passes; "
+    rp_gbs = (st["rref_pass_bytes"] / (st["rref_pass_ms"] / 1e3) / 1e9) if st["rref_pass_ms"] > 0 else None
+    roofline = {"kernel": "update_pipe_kernel (tabulated trailing update of the PLE stripes; "
                           + ("paired 64-byte tiles)" if args.paired else "wide 128-byte tiles)"),
                 "bound": "hbm", "achieved": upd_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (upd_gbs / hbm) if upd_gbs else None, "peak_kind": hbm_kind,
                 "frac_of_nominal_8000": (upd_gbs / 8000.0) if upd_gbs else None,
                 "traffic": traffic, "algorithmic_bytes_per_launch": upd_per_launch_bytes,
-                "traffic_source": (f"{ratio_src}: ncu dram__bytes_read.sum + dram__bytes_write.sum over "
-                                   f"every update launch of one captured 65536^2 step, {ratio:.4f} DRAM bytes "
-                                   f"per algorithmic byte, times this run's algorithmic bytes per launch")
+                "traffic_source": (f"{ratio_src}: ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                   f"update_pipe_kernel launches of a 32768^2 PLE, {ratio:.4f} DRAM bytes per "
+                                   f"algorithmic byte, times this run's algorithmic bytes per launch")
                                   if ratio else None,
                 "launches_per_step": st["update_launches"] / args.steps,
                 "timed_launches": st["update_timed_launches"],
                 "update_share_of_step_diagnostic": None,
                 "kernel_ms_per_step_diagnostic": {k: sd[k + "_ms"] / diag_steps
-                                                  for k in ("update", "panel", "prep", "rref_prep", "other")},
+                                                  for k in ("update", "panel", "prep", "rref_prep", "rref_pass",
+                                                            "other")},
                 "algorithmic_bytes_per_step_diagnostic": sd["update_bytes"] / diag_steps,
+                "rref_pass_kernel": {"achieved_gbs": rp_gbs, "frac": (rp_gbs / hbm) if rp_gbs else None,
+                                     "launches_per_step": st["rref_pass_launches"] / args.steps,
+                                     "algorithmic_bytes_per_step": st["rref_pass_bytes"] /
+                                     max(st["rref_pass_timed_launches"], 1) * st["rref_pass_launches"] /
+                                     args.steps},
                 "note": "achieved = algorithmic bytes / CUDA-event time of every 7th update launch "
                         "of the timed steps (events on the launching stream); the per-kind breakdown "
-                        "comes from a separate pass with every launch bracketed by events (panels "
-                        "overlap the update on a side stream)"}
+                        "comes from a separate pass with every launch bracketed by events (the update "
+                        "runs on a side stream beside the panels); the RREF stripe passes run in their "
+                        "own kernel (rref_pass_kernel), counted apart"}
     roofline["update_share_of_step_diagnostic"] = (roofline["kernel_ms_per_step_diagnostic"]["update"] /
                                                    per_step_ms) if per_step_ms > 0 else None
 
@@ -741,6 +799,33 @@ def run_ours(args):
                 "m4ri_rref_ms": statistics.median(mt[1:]),
                 "ple_ms": statistics.median(pt), "ple_gbitops": work_bits(ns, ns, rs) / statistics.median(pt) / 1e6}
         del ps, ws
+    # ---- the own tensor-core GEMM alone: the 32768^3 GF(2) product, against
+    # the FP4 peak (the measured bf16 peak times the nominal FP4 / bf16 ratio)
+    gemm = None
+    if args.side and rank == 0:
+        ng = 32768
+        Ag = torch.from_numpy(gi.bernoulli_matrix(ng, ng, gi.BASE_SEED + 7).view(np.int64)).to(dev)
+        Bg = torch.from_numpy(gi.bernoulli_matrix(ng, ng, gi.BASE_SEED + 8).view(np.int64)).to(dev)
+        Cg = torch.empty_like(Ag)
+        h.mul(Cg, Ag, Bg, ng, ng, ng)
+        gt = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.mul(Cg, Ag, Bg, ng, ng, ng)
+            b.record(stream)
+            torch.cuda.synchronize()
+            gt.append(a.elapsed_time(b))
+        gms = statistics.median(gt)
+        bf16, bf16_kind = bf16_peak()
+        fp4_peak = bf16 * 6.0 if bf16 else None
+        tf = 2.0 * ng ** 3 / (gms / 1e3) / 1e12
+        gemm = {"kernel": "gemm_f4_kernel (tcgen05 kind::mxf4, TMA-fed, parities from tensor memory)",
+                "workload": f"C = A B over GF(2), {ng}^3, Bernoulli(1/2); bit expansion included",
+                "ms": gms, "bound": "tensor", "achieved": tf, "unit": "TFLOP/s (2 m k n, exact 0/1 FP4)",
+                "peak": fp4_peak, "frac": (tf / fp4_peak) if fp4_peak else None,
+                "peak_kind": f"{bf16_kind} bf16 x 6 (nominal FP4 13.5 / bf16 2.25 PFLOP/s)"}
+        del Ag, Bg, Cg
     # PLE alone at the main size
     ple_ms = m4ri_ms = None
     if rank == 0 and args.side:
@@ -819,7 +904,8 @@ def run_ours(args):
                                          "updates as one-by-one row additions (no tables, no blocked products, "
                                          "no look-ahead)",
                            "no_lookahead_ms": plain_ms},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "served": served,
+                "roofline": roofline, "gemm_roofline": gemm, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+                "served": served,
                 "sparse": sparse,
                 "rref_65536_ms": max_ms / args.steps if n == 65536 else None,
                 "ple_65536_ms": ple_ms if n == 65536 else None,
@@ -832,19 +918,74 @@ def run_ours(args):
     return 0
 
 
+def run_only(args):
+    """One call of one workload at --size (default 32768), for profilers: ple /
+    rref (dense Bernoulli(1/2) square), mul (--size^3 product), batched (the
+    4096-matrix batch, two calls).  Prints one line, no timing claims."""
+    import torch
+    import gf2inputs as gi
+    import paper_1111_6549_gb300 as g
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    h = g.Handle(0)
+    n = args.n if args.n is not None else N_SIDE
+    if args.only in ("ple", "rref"):
+        A = torch.from_numpy(gi.dense_square(n).view(np.int64)).to(dev)
+        Q = torch.empty(n, dtype=torch.int64, device=dev)
+        if args.only == "ple":
+            P = torch.empty(n, dtype=torch.int64, device=dev)
+            r = h.ple(A, n, n, P, Q)
+        else:
+            r = h.rref(A, n, n, Q)
+        print(f"{args.only} {n}x{n} rank {r}")
+    elif args.only == "mul":
+        Ag = torch.from_numpy(gi.bernoulli_matrix(n, n, gi.BASE_SEED + 7).view(np.int64)).to(dev)
+        Bg = torch.from_numpy(gi.bernoulli_matrix(n, n, gi.BASE_SEED + 8).view(np.int64)).to(dev)
+        Cg = torch.empty_like(Ag)
+        for _ in range(2):
+            h.mul(Cg, Ag, Bg, n, n, n)
+        torch.cuda.synchronize()
+        print(f"mul {n}^3 done")
+    else:
+        specs = gi.batch_recipe(count=4096)
+        mats = [gi.batch_matrix(sp) for sp in specs]
+        offs, tot = [], 0
+        for A in mats:
+            offs.append(tot)
+            tot += A.size
+        host = np.zeros(tot, dtype=np.uint64)
+        for A, o in zip(mats, offs):
+            host[o:o + A.size] = A.ravel()
+        work = torch.from_numpy(host.view(np.int64)).to(dev)
+        maxm = max(sp["m"] for sp in specs)
+        P = torch.empty((len(specs), maxm), dtype=torch.int64, device=dev)
+        Q = torch.empty((len(specs), maxm), dtype=torch.int64, device=dev)
+        R = torch.zeros(len(specs), dtype=torch.int64, device=dev)
+        items = [(work[o:o + A.size].view(A.shape[0], A.shape[1]), sp["m"], sp["n"], P[b], Q[b], R[b:b + 1])
+                 for b, (sp, o, A) in enumerate(zip(specs, offs, mats))]
+        for _ in range(2):
+            h.ple_batched(items)
+        torch.cuda.synchronize()
+        print(f"batched 4096 matrices, rank sum {int(R.sum())}")
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--size", dest="n", type=int, default=N_MAIN)
+    ap.add_argument("--size", dest="n", type=int, default=None)
     ap.add_argument("--no-side", dest="side", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--only", choices=("ple", "rref", "mul", "batched"), default=None,
+                    help="one call of one workload at --size (default 32768) for a profiler; no timing")
     ap.add_argument("--served-seconds", type=float, default=2.0,
                     help="seconds of Poisson arrivals per offered rate in the served sweep (30: the full sweep)")
     ap.add_argument("--served-slots", type=int, default=6, help="execution slots of the solve server")
@@ -862,6 +1003,10 @@ def main():
     ap.add_argument("--tc-compare", action="store_true",
                     help="only compare the tensor-core and table forms (product, PLE update)")
     args = ap.parse_args()
+    if args.only:
+        return run_only(args)
+    if args.n is None:
+        args.n = N_MAIN
     if args.impl == "reference":
         return run_reference(args)
     if args.tc_compare:

@@ -389,6 +389,12 @@ typedef struct gf2_stats {
     double  rref_prep_ms;
     double  other_ms;
     int64_t update_timed_launches;/* update launches timed while profiling     */
+    double  rref_pass_ms;         /* fused RREF stripe passes (rref_pass_kernel,
+                                     counted apart from the update): event time,
+                                     algorithmic bytes, launches, timed launches */
+    double  rref_pass_bytes;
+    int64_t rref_pass_launches;
+    int64_t rref_pass_timed_launches;
 } gf2_stats;
 /* Per-launch event timing: 0 off, 1 the update kernel only, 2 every kernel,
    3 every 7th update launch (only those add to update_ms and update_bytes),
@@ -400,7 +406,8 @@ int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);
 int gf2_reset_stats(gf2_handle_t handle);
 /* Profiling level 4: the timed launches since the last reset, in launch
    order, as (kind, start ms, end ms) triples in out (host, 3 * max_records
-   doubles); kind 0 update, 1 panel, 2 prep, 3 RREF prep, 4 other; times from
+   doubles); kind 0 update, 1 panel, 2 prep, 3 RREF prep, 4 other, 5 fused
+   RREF pass; times from
    CUDA events recorded on each launch's stream, relative to the first one.
    *count = the number of records (more than max_records: the rest are not
    written).  Synchronises the stream. */

@@ -42,7 +42,9 @@ class _Stats(ctypes.Structure):
                 ("update_ms", ctypes.c_double), ("update_bytes", ctypes.c_double),
                 ("panel_fallbacks", ctypes.c_int64), ("panel_ms", ctypes.c_double),
                 ("prep_ms", ctypes.c_double), ("rref_prep_ms", ctypes.c_double),
-                ("other_ms", ctypes.c_double), ("update_timed_launches", ctypes.c_int64)]
+                ("other_ms", ctypes.c_double), ("update_timed_launches", ctypes.c_int64),
+                ("rref_pass_ms", ctypes.c_double), ("rref_pass_bytes", ctypes.c_double),
+                ("rref_pass_launches", ctypes.c_int64), ("rref_pass_timed_launches", ctypes.c_int64)]
 
 
 class SolveJob(ctypes.Structure):

@@ -47,7 +47,9 @@ struct gf2_handle {
     std::vector<cudaEvent_t> ev_free;
     struct Pending { cudaEvent_t e0, e1; int kind; };
     std::vector<Pending> ev_pending;
-    double kind_ms[5] = {0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other
+    double kind_ms[6] = {0, 0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other, rref pass
+    int64_t rpass_launches = 0;    // fused RREF pass launches (rref_pass_kernel)
+    int64_t rpass_timed = 0;
     cudaEvent_t tl_ref = nullptr;  // profiling level 4: the timeline's time origin (first timed event)
     std::vector<double> timeline;  // level 4: (kind, start ms, end ms) per timed launch
     BatchTune btune{};             // batched kernel: table configuration per size class
@@ -87,6 +89,7 @@ constexpr size_t SM_FALLBACK = 12; // int32 block-wide panel count
 constexpr size_t SM_BYTES = 16;    // uint64 algorithmic bytes of update launches
 constexpr size_t SM_FLAG = 24;     // int32 solve inconsistency flag
 constexpr size_t SM_STATUS = 28;   // int32 solve status
+constexpr size_t SM_BYTES2 = 32;   // uint64 algorithmic bytes of fused RREF passes
 constexpr size_t SM_BYTES_TOTAL = 256;
 
 int64_t *r_dev(gf2_handle *h) { return reinterpret_cast<int64_t *>(h->small + SM_RANK); }
@@ -181,7 +184,7 @@ int grow(char **buf, size_t *cap, size_t need, cudaStream_t st)
         if (e_ != cudaSuccess) { cudaGetLastError(); return GF2_ECUDA; } \
     } while (0)
 
-enum { K_UPDATE = 0, K_PANEL = 1, K_PREP = 2, K_RPREP = 3, K_OTHER = 4 };
+enum { K_UPDATE = 0, K_PANEL = 1, K_PREP = 2, K_RPREP = 3, K_OTHER = 4, K_RPASS = 5 };
 
 // With profiling on, brackets one launch with a pair of events on the
 // handle's stream; the elapsed times are summed per kernel kind later.
@@ -193,7 +196,9 @@ struct Timed {
     Timed(gf2_handle *h_, int kind_, cudaStream_t st_ = nullptr, bool enable = true)
         : h(h_), kind(kind_), st(st_ ? st_ : h_->stream)
     {
-        if (!enable || h->profiling == 0 || (h->profiling != 2 && h->profiling != 4 && kind != K_UPDATE)) return;
+        if (!enable || h->profiling == 0 ||
+            (h->profiling != 2 && h->profiling != 4 && kind != K_UPDATE && kind != K_RPASS))
+            return;
         e0 = take();
         if (e0) cudaEventRecord(e0, st);
     }
@@ -223,11 +228,15 @@ constexpr int64_t UPD_SAMPLE = 7;
 int launch_update_counted(gf2_handle *h, const UpdArgs &a_in, cudaStream_t st = nullptr)
 {
     if (!st) st = h->stream;
-    const bool timed = h->profiling != 3 || h->upd_launches % UPD_SAMPLE == 0;
-    Timed t(h, K_UPDATE, st, timed);
+    // the fused RREF passes (their own kernel) are counted and timed apart
+    const bool rpass = a_in.rref_fused != 0;
+    const int64_t nth = rpass ? h->rpass_launches : h->upd_launches;
+    const bool timed = h->profiling != 3 || nth % UPD_SAMPLE == 0;
+    Timed t(h, rpass ? K_RPASS : K_UPDATE, st, timed);
     UpdArgs a = a_in;
+    if (rpass && a.bytes) a.bytes = reinterpret_cast<unsigned long long *>(h->small + SM_BYTES2);
     if (!timed) a.bytes = nullptr;
-    else if (h->profiling) h->upd_timed += 1;
+    else if (h->profiling) (rpass ? h->rpass_timed : h->upd_timed) += 1;
     a.err = err_dev(h);
     a.wide = h->wide_update ? 1 : 0;
     a.naive = h->naive_update ? 1 : 0;
@@ -247,7 +256,8 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in, cudaStream_t st = 
     if (tc) CK(launch_update_tc(st, a, h->num_sms));
     else CK(launch_update(st, a, h->num_sms));
     h->launches += 1;
-    h->upd_launches += 1;
+    if (rpass) h->rpass_launches += 1;
+    else h->upd_launches += 1;
     return GF2_OK;
 }
 
@@ -1668,6 +1678,12 @@ int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
     out->prep_ms = h->kind_ms[K_PREP];
     out->rref_prep_ms = h->kind_ms[K_RPREP];
     out->other_ms = h->kind_ms[K_OTHER];
+    out->rref_pass_ms = h->kind_ms[K_RPASS];
+    out->rref_pass_launches = h->rpass_launches;
+    out->rref_pass_timed_launches = h->rpass_timed;
+    unsigned long long b2 = 0;
+    CK(cudaMemcpy(&b2, h->small + SM_BYTES2, 8, cudaMemcpyDeviceToHost));
+    out->rref_pass_bytes = (double)b2;
     out->update_bytes = (double)bytes;
     out->panel_fallbacks = fb;
     return GF2_OK;
@@ -1699,6 +1715,9 @@ int gf2_reset_stats(gf2_handle_t h)
     h->launches = 0;
     h->upd_launches = 0;
     h->upd_timed = 0;
+    h->rpass_launches = 0;
+    h->rpass_timed = 0;
+    CK(cudaMemset(h->small + SM_BYTES2, 0, 8));
     for (double &x : h->kind_ms) x = 0.0;
     CK(cudaMemset(h->small + SM_FALLBACK, 0, 12));
     return GF2_OK;

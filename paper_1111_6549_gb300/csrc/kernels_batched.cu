@@ -166,7 +166,7 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
             __syncthreads();
             const int rbar = sh.rbar;
             if (rbar == 0) continue;
-            if (warp == 0) warp_lower_inverse(sh.L, rbar, sLinv);
+            if (warp == 0) warp_lower_inverse_blocked(sh.L, rbar, sLinv);
             for (int p = tid; p < rbar; p += BATCH_THREADS) {
                 it.P[r + p] = r + sh.t[p];
                 it.Q[r + p] = c + sh.j[p];

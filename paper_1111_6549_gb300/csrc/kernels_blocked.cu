@@ -124,7 +124,7 @@ trsm_leaf_prep_kernel(const uint64_t *__restrict__ Lt, int64_t ldt, int64_t kb, 
     const int nt = (int)min((int64_t)KS, kb - 64 * (int64_t)t);
     if (tid < KS) sL[tid] = (tid < nt) ? (Lt[(64 * (int64_t)t + tid) * ldt + t] & ((1ull << tid) - 1ull)) : 0ull;
     __syncthreads();
-    if (tid < 32) warp_lower_inverse(sL, nt, sM);
+    if (tid < 32) warp_lower_inverse_blocked(sL, nt, sM);
     __syncthreads();
     // byte tables of the block inverse's rows: tab[b][e] = XOR of rows 8 b + q, bits q of e
     for (int e2 = tid; e2 < 8 * 256; e2 += blockDim.x) {

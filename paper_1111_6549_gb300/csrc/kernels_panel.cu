@@ -102,35 +102,32 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
     __shared__ uint64_t sMinv[KS], sLinv[KS];          // shared copies for the prep tables
     if (warp == 1) {
         // U11^-1 for the RREF recovery, U11[p][q] = E11[p] at column qbar[q]
-        // (unit upper triangular): lane-parallel backward substitution per
-        // column, rows collected by ballot.  Runs beside warp 0's L11^-1.
-        __shared__ uint64_t sU[KS];
-        for (int p = lane; p < rbar; p += 32) {
-            const uint64_t e = sh.E[p];
+        // (unit upper triangular): reversing the order of rows and columns
+        // makes it unit lower triangular, inverted in 32 x 32 blocks beside
+        // warp 0's L11^-1
+        __shared__ uint64_t sU[KS], sUi[KS];
+        for (int p = lane; p < KS; p += 32) {
             uint64_t u = 0;
+            if (p < rbar) {
+                const uint64_t e = sh.E[p];
 #pragma unroll 16
-            for (int q = 0; q < KS; ++q)
-                u |= (q < rbar ? ((e >> (sh.j[q] & 63)) & 1ull) : 0ull) << q;
-            sU[p] = u;
+                for (int q = 0; q < KS; ++q)
+                    u |= (q < rbar ? ((e >> (sh.j[q] & 63)) & 1ull) : 0ull) << q;
+            } else {
+                u = 1ull << p;
+            }
+            sU[63 - p] = __brevll(u);                       // row 63 - p of the reversed matrix
         }
         __syncwarp();
-        uint64_t x0 = 0, x1 = 0;
-        for (int p = rbar - 1; p >= 0; --p) {
-            const uint64_t up = sU[p];
-            x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(up & x0)) & 1) << p;
-            x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(up & x1)) & 1) << p;
-        }
-        for (int p = 0; p < rbar; ++p) {
-            const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
-            const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
-            if (lane == 0) {
-                const uint64_t v = ((uint64_t)hi << 32) | lo;
-                d->Minv[p] = v;
-                sMinv[p] = v;
-            }
+        warp_lower_inverse_blocked(sU, KS, sUi);
+        __syncwarp();
+        for (int p = lane; p < rbar; p += 32) {
+            const uint64_t v = __brevll(sUi[63 - p]);
+            d->Minv[p] = v;
+            sMinv[p] = v;
         }
     }
-    if (warp == 0) warp_lower_inverse(sh.L, rbar, d->Linv, sLinv);
+    if (warp == 0) warp_lower_inverse_blocked(sh.L, rbar, d->Linv, sLinv);
     for (int p = tid; p < rbar; p += blockDim.x) {
         P[r + p] = r + sh.t[p];
         Q[r + p] = c + sh.j[p];

@@ -257,25 +257,25 @@ struct RowBatch {
     int64_t ri[PIPE_RPT];
 };
 
-template <bool WIDE>
-__global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
+// The body of the pipelined table kernels; FUSED: the RREF pass with the
+// block reduction fused in (rref_pass_kernel, wide tiles only).
+template <bool WIDE, bool FUSED>
+__device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
 {
-    pdl_wait();
-    pdl_trigger();
-    extern __shared__ __align__(16) uint64_t T[];
     __shared__ const uint64_t *sGen[KS];
     // fused RREF passes: the stripe's raw pivot rows and its reduced rows by
     // pivot column, one tile wide; U11^-1
-    __shared__ __align__(16) uint64_t sRaw[WIDE ? KS * WT : 1], sGc[WIDE ? KS * WT : 1];
-    __shared__ uint64_t sMinv[KS];
-    __shared__ int8_t sCol[KS];
+    __shared__ __align__(16) uint64_t sRaw[FUSED ? KS * WT : 1], sGc[FUSED ? KS * WT : 1];
+    __shared__ uint64_t sMinv[FUSED ? KS : 1];
+    __shared__ int8_t sCol[FUSED ? KS : 1];
 
     int64_t row_lo, row_hi, w_lo;
     const int64_t W = a.W;
     int64_t r = 0;
     int maxpos = -1, nS = 0, rbar_m = 0;
     const StripeDesc *d = a.desc;
-    const bool fused = WIDE && a.mode == UPD_RREF && a.rref_fused;
+    constexpr bool fused = FUSED;
+    static_assert(!FUSED || WIDE, "the fused RREF pass uses wide tiles");
     if (fused) rref_side_jobs(a, W);
     if (a.mode == UPD_PLE) {
         const int rbar = d->rbar;
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
         if (fused) {
             fused_g(wbase);
             build_wide_tables_smem(T, sGc);
-        } else if (WIDE) build_wide_tables(T, sGen, wbase, W);
+        } else if (WIDE) build_wide_tables(T, sGen, wbase, W, w_lo);
         else build_tables(T, sGen, wbase, W);
         __syncthreads();
 
@@ -513,6 +513,27 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     }
 }
 
+template <bool WIDE>
+__global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) uint64_t T[];
+    update_pipe_body<WIDE, false>(a, T);
+}
+
+// One RREF stripe pass with the stripe's block reduction fused in (see
+// UpdArgs::rref_fused): the table update of the rows above the stripe, the
+// reduced pivot rows formed per tile, and the neighbouring passes' write-back
+// and index snapshot.
+__global__ void __launch_bounds__(UPD_THREADS, 1) rref_pass_kernel(UpdArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) uint64_t T[];
+    update_pipe_body<true, true>(a, T);
+}
+
 
 // ----------------------------------------------------------------------------
 // Naive form, the plain baseline: no tables.  One thread per (row, word) adds
@@ -599,6 +620,9 @@ cudaError_t setup_update_kernel()
     e = cudaFuncSetAttribute(update_pipe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(WIDE_TAB_WORDS * sizeof(uint64_t)));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rref_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(WIDE_TAB_WORDS * sizeof(uint64_t)));
+    if (e != cudaSuccess) return e;
     e = setup_update_tma_kernel();
     if (e != cudaSuccess) return e;
     return setup_prep_kernel();   // the prep kernel's 48 KiB of tables
@@ -627,6 +651,11 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
         if (grid < 2) grid = 2;
         if (a.tmap)
             return launch_update_tma(st, a, grid);
+        if (a.rref_fused && a.wide) {
+            int gw = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
+            return launch_kernel(rref_pass_kernel, dim3(gw), dim3(UPD_THREADS), WIDE_TAB_WORDS * sizeof(uint64_t), st,
+                                 a);
+        }
         if (a.wide) {
             int gw = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
             return launch_kernel(update_pipe_kernel<true>, dim3(gw), dim3(UPD_THREADS),

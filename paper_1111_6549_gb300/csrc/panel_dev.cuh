@@ -321,29 +321,6 @@ __device__ __forceinline__ void panel_block(const uint64_t *__restrict__ A, int6
     __syncthreads();
 }
 
-// Rows of L11^-1 (L11 unit lower triangular, rows Lrows[0..rbar)), by one
-// warp: forward substitution per column (lane owns columns lane and
-// lane + 32), rows collected by ballot; lane 0 writes out[p] (and out2[p]).
-__device__ __forceinline__ void warp_lower_inverse(const uint64_t *Lrows, int rbar, uint64_t *out,
-                                                   uint64_t *out2 = nullptr)
-{
-    const int lane = threadIdx.x & 31;
-    uint64_t x0 = 0, x1 = 0;
-    for (int p = 0; p < rbar; ++p) {
-        const uint64_t Lp = Lrows[p];
-        x0 |= (uint64_t)((((p == lane) ? 1 : 0) ^ __popcll(Lp & x0)) & 1) << p;
-        x1 |= (uint64_t)((((p == lane + 32) ? 1 : 0) ^ __popcll(Lp & x1)) & 1) << p;
-    }
-    for (int p = 0; p < rbar; ++p) {
-        const unsigned lo = __ballot_sync(0xffffffffu, (x0 >> p) & 1ull);
-        const unsigned hi = __ballot_sync(0xffffffffu, (x1 >> p) & 1ull);
-        if (lane == 0) {
-            const uint64_t v = ((uint64_t)hi << 32) | lo;
-            out[p] = v;
-            if (out2) out2[p] = v;
-        }
-    }
-}
 
 // Fast path over four warps (threads 0..127 of the block, every one of them
 // must call it): the same search as panel_window, with window slot i held by
@@ -435,6 +412,59 @@ __device__ __forceinline__ void panel_window4(const uint64_t *__restrict__ A, in
         }
     }
     if (slot == 0) { sh.fail = fail ? 1 : 0; sh.rbar = p; }
+}
+
+// Inverse of a 64 x 64 unit lower triangular matrix by one warp, in 32 x 32
+// blocks: with L = [L1 0; C L2], L^-1 = [L1^-1 0; L2^-1 C L1^-1  L2^-1].
+// Lane l forms column l of L1^-1 and of L2^-1 by forward substitution (two
+// independent 32-step chains), then column l of the lower-left block as
+// L2^-1 (C (column l of L1^-1)) by parities; rows come out by ballot.
+// Lrows[p] (p < n) holds row p's strictly lower bits (bits at or above the
+// diagonal are ignored); rows p >= n count as identity rows.  Writes row p
+// of L^-1 to out[p] (and out2[p]) for p < n.
+__device__ __forceinline__ void warp_lower_inverse_blocked(const uint64_t *Lrows, int n, uint64_t *out,
+                                                           uint64_t *out2 = nullptr)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    auto row = [&](int p) -> uint64_t { return p < n ? (Lrows[p] & ((1ull << p) - 1ull)) : 0ull; };
+    uint32_t x0 = 0, x1 = 0;                        // column lane of L1^-1, of L2^-1
+#pragma unroll 8
+    for (int p = 0; p < 32; ++p) {
+        const uint32_t l1 = (uint32_t)row(p);
+        const uint32_t l2 = (uint32_t)(row(32 + p) >> 32);
+        x0 |= (uint32_t)((((p == lane) ? 1 : 0) ^ __popc(l1 & x0)) & 1) << p;
+        x1 |= (uint32_t)((((p == lane) ? 1 : 0) ^ __popc(l2 & x1)) & 1) << p;
+    }
+    // Y = C (column lane of L1^-1), C = rows 32..63, columns 0..31
+    uint32_t y = 0;
+#pragma unroll 8
+    for (int p = 0; p < 32; ++p) y |= (uint32_t)(__popc((uint32_t)row(32 + p) & x0) & 1) << p;
+    // rows of L2^-1 by ballot, then the lower-left column L2^-1 Y
+    uint32_t z = 0;
+    uint32_t r1lo = 0, r2lo = 0, r2hi = 0;
+#pragma unroll 8
+    for (int p = 0; p < 32; ++p) {
+        const uint32_t l2inv_p = __ballot_sync(FULL, (x1 >> p) & 1u);
+        z |= (uint32_t)(__popc(l2inv_p & y) & 1) << p;
+    }
+    // row p of L^-1: [L1^-1 row p | 0]; row 32 + p: [lower-left row p | L2^-1 row p]
+#pragma unroll 8
+    for (int p = 0; p < 32; ++p) {
+        const uint32_t a = __ballot_sync(FULL, (x0 >> p) & 1u);
+        const uint32_t b = __ballot_sync(FULL, (z >> p) & 1u);
+        const uint32_t c = __ballot_sync(FULL, (x1 >> p) & 1u);
+        if (lane == p) { r1lo = a; r2lo = b; r2hi = c; }
+    }
+    const uint64_t v0 = (uint64_t)r1lo, v1 = ((uint64_t)r2hi << 32) | r2lo;
+    if (lane < n) {
+        out[lane] = v0;
+        if (out2) out2[lane] = v0;
+    }
+    if (lane + 32 < n) {
+        out[lane + 32] = v1;
+        if (out2) out2[lane + 32] = v1;
+    }
 }
 
 }  // namespace gf2

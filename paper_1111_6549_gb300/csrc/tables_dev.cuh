@@ -42,14 +42,16 @@ __device__ __forceinline__ void build_tables(uint64_t *T, const uint64_t *const 
 
 // Wide form: 128-byte tiles (WT words), table t < 8 holding the 128
 // combinations of generator rows 7t .. 7t+6, table 8 the 256 combinations of
-// rows 56 .. 63.  Work items are (32-entry segment, word): 8 x 4 + 8 = 40
+// rows 56 .. 63; only the words [w_lo, W) of the tile are built.  Work items are (32-entry segment, word): 8 x 4 + 8 = 40
 // segments x 16 words = 640 items over the block's threads; each item walks
 // its segment in Gray-code order (31 additions after the segment's base).
 __device__ __forceinline__ void build_wide_tables(uint64_t *T, const uint64_t *const *gen, int64_t wbase,
-                                                  int64_t W)
+                                                  int64_t W, int64_t w_lo = 0)
 {
     for (int item = threadIdx.x; item < 40 * WT; item += blockDim.x) {
         const int w = item % WT, seg = item / WT;
+        // words outside [w_lo, W) are never stored back: their entries may stay stale
+        if (wbase + w < w_lo || wbase + w >= W) continue;
         const int t = seg < 32 ? seg >> 2 : 8;       // table
         const int q = seg < 32 ? seg & 3 : seg - 32; // segment: index bits 5.. of the table
         const int nb = t < 8 ? 7 : 8;                // index bits of the table
