@@ -610,6 +610,23 @@ def tc_compare(args):
         res["identical"] = bool(torch.equal(outs[0], outs[1]))
         out["ple"].append(res)
     h.set_option(g.OPT_TC_UPDATE, 0)
+    # the carriers alone: one CTA per SM issuing back-to-back MMAs of each
+    # form on operands already in place (AND-population counts per second;
+    # each launch's count is checked against the exact value)
+    out["carriers"] = {}
+    for name, c, per in (("fp4_tcgen05_mxf4", g.CARRIER_FP4, 64), ("fp8_tcgen05_f8f6f4", g.CARRIER_FP8, 64),
+                         ("b1_mma_sync_and_popc", g.CARRIER_B1, 256)):
+        t0 = time.time()
+        g.carrier_rate(c, 1024)
+        est_ms = (time.time() - t0) * 1e3 / 1024
+        lim = (2 ** 31 // 256 - 1) if c == g.CARRIER_B1 else (2 ** 24 // 64 - 1)
+        iters = int(min(lim, max(1024, 40.0 / max(est_ms, 1e-6))))
+        rates = []
+        for _ in range(3):
+            rate, cnt = g.carrier_rate(c, iters)
+            assert cnt == iters * per, (name, cnt, iters * per)
+            rates.append(rate)
+        out["carriers"][name] = {"iters": iters, "and_popc_per_s": max(rates)}
     h.close()
     print(json.dumps(out), flush=True)
     return 0

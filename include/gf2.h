@@ -244,10 +244,12 @@ int gf2_rref_host(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_
  * nothing.  Scratch: one fixed array of about 0.5 MiB inside the library,
  * held on every GPU that loads the library until the process exits.  The
  * first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  Every
- * call shares the array and re-initialises what must start from a known
- * state; calls whose work overlaps on the GPU race on it.  Synchronises the
- * stream before returning.
+ * device address.  Every call shares the array and re-initialises what must
+ * start from a known state; calls whose work overlaps on the GPU race on it.
+ * Synchronises the stream before returning (it reads the rank and pivot
+ * counts back to the host between launches), so it can never be captured
+ * into a CUDA graph: on a stream that is capturing it returns GF2_EINVAL and
+ * enqueues nothing.
  */
 int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_words, int64_t *P, int64_t *Q,
                     int64_t *rank, void *stream);

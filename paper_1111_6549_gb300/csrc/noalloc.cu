@@ -120,6 +120,10 @@ extern "C" int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_wor
     int sdev = dev;
     NA_CK(cudaStreamGetDevice(st, &sdev));
     if (sdev != dev) return GF2_EINVAL;
+    // the call synchronises the stream between launches: it cannot be captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NA_CK(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return GF2_EINVAL;
 
     char *base = nd->base;
     int64_t *r_dev = reinterpret_cast<int64_t *>(base + OFF_SMALL);

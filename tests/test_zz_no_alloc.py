@@ -90,3 +90,28 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     A = vec_dev(8)
     assert f(A.data_ptr(), 4097, 64, 1, A.data_ptr(), A.data_ptr(), ctypes.byref(rank), None) == 1
     assert f(A.data_ptr(), 64, 4097, 65, A.data_ptr(), A.data_ptr(), ctypes.byref(rank), None) == 1
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises its stream, so it must not be captured: on a
+    capturing stream it returns GF2_EINVAL before enqueueing anything."""
+    import torch
+    import paper_1111_6549_gb300 as g
+    m = n = 256
+    A = gi.bernoulli_matrix(m, n, seed=11)
+    _ple_noalloc(A, m, n)                       # first call on the device: address lookup
+    L = g.load()
+    f = L.gf2_ple_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    dA = to_dev(A)
+    P, Q = vec_dev(m), vec_dev(n)
+    rank = ctypes.c_int64(-1)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        rc = f(dA.data_ptr(), m, n, gi.words_for(n), P.data_ptr(), Q.data_ptr(), ctypes.byref(rank),
+               ctypes.c_void_p(s.cuda_stream))
+        P.add_(0)                               # keep the captured graph non-empty
+    assert rc == 1                              # GF2_EINVAL
+    del graph
