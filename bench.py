@@ -567,8 +567,8 @@ def tc_compare(args):
         return statistics.median(ts)
 
     out = {"mode": "tc_compare", "mul": [], "ple": []}
-    for (m, k, n) in [(16384, 64, 16384), (16384, 1024, 16384), (16384, 2048, 16384), (16384, 4096, 16384),
-                      (16384, 16384, 16384), (32768, 32768, 32768)]:
+    for (m, k, n) in [(16384, 64, 16384), (16384, 256, 16384), (16384, 512, 16384), (16384, 1024, 16384),
+                      (16384, 2048, 16384), (16384, 4096, 16384), (16384, 16384, 16384), (32768, 32768, 32768)]:
         A = torch.from_numpy(gi.bernoulli_matrix(m, k, 1).view(np.int64)).to(dev)
         B = torch.from_numpy(gi.bernoulli_matrix(k, n, 2).view(np.int64)).to(dev)
         C = torch.zeros((m, gi.words_for(n)), dtype=torch.int64, device=dev)
@@ -586,7 +586,7 @@ def tc_compare(args):
         res["identical"] = all(bool(torch.equal(outs["table"], v)) for v in outs.values())
         out["mul"].append(res)
     h.set_option(g.OPT_TC_MUL, 0)
-    h.set_option(g.OPT_MUL_GEMM_MIN_K, 4096)
+    h.set_option(g.OPT_MUL_GEMM_MIN_K, 1024)
     h.set_option(g.OPT_MUL_GEMM_FORMAT, 0)
     for nn in (16384, 32768):
         A = torch.from_numpy(gi.dense_square(nn).view(np.int64)).to(dev)

@@ -120,7 +120,9 @@ int gf2_rref_m4ri_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, 
  *   C = A B (accumulate = 0) or C ^= A B (accumulate != 0).
  *   A device m x k (lda words), B device k x n (ldb), C device m x n (ldc).
  *   C must not overlap A or B.  Asynchronous.
- * Inner dimensions below GF2_OPT_MUL_GEMM_MIN_K (default 4096) use the
+ * Inner dimensions below GF2_OPT_MUL_GEMM_MIN_K (default 1024, the measured
+ * crossover on GB300: at 16384 x k x 16384 the tables win at k = 512, the
+ * GEMM at k = 1024) use the
  * tabulated row combinations, 64 columns of A per pass over C; larger ones
  * the library's own block-scaled FP4 tcgen05 GEMM (TMA-fed, parities taken
  * from tensor memory in its epilogue); GF2_OPT_TC_MUL selects the older
@@ -315,7 +317,7 @@ int gf2_server_destroy(gf2_server_t server);
  *                      expanded to FP4 0/1, the library's own tcgen05
  *                      block-scaled FP4 kernel counting in tensor memory and
  *                      XORing each count's parity into C; below it, the
- *                      Four-Russians tables (default 4096)
+ *                      Four-Russians tables (default 1024)
  *   GF2_OPT_PLE_BLOCK  value > 0 (a multiple of 64): PLE (and everything
  *                      built on it) decomposes value columns at a time with
  *                      the updates inside the block, then applies the
@@ -358,6 +360,13 @@ int gf2_server_destroy(gf2_server_t server);
  *                      the device for its completion, which hides the launch
  *                      latency between the many short dependent kernels
  *                      (default on; 0: plain stream ordering)
+ *   GF2_OPT_PLE_RECURSIVE  with a PLE block width in effect: 1 decomposes
+ *                      by Algorithm 3's recursion (Section 3.3) -- the columns
+ *                      halved until a half is no wider than the block width,
+ *                      each left half's row moves, TRSM and product applied
+ *                      to its right sibling's columns only -- instead of
+ *                      iterating over the blocks left to right, each block's
+ *                      trailing update reaching the row end (default 0)
  * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
@@ -375,6 +384,7 @@ int gf2_server_destroy(gf2_server_t server);
 #define GF2_OPT_WIDE_UPDATE     9
 #define GF2_OPT_NAIVE_UPDATE    10
 #define GF2_OPT_PDL             11
+#define GF2_OPT_PLE_RECURSIVE   12
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */

@@ -25,7 +25,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
 (OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE, OPT_TMA_UPDATE, OPT_MUL_GEMM_MIN_K, OPT_PLE_BLOCK,
- OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE, OPT_NAIVE_UPDATE, OPT_PDL) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11
+ OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE, OPT_NAIVE_UPDATE, OPT_PDL,
+ OPT_PLE_RECURSIVE) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
 BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
 CARRIER_B1, CARRIER_FP4, CARRIER_FP8 = 1, 4, 8

@@ -54,13 +54,14 @@ struct gf2_handle {
     std::vector<double> timeline;  // level 4: (kind, start ms, end ms) per timed launch
     BatchTune btune{};             // batched kernel: table configuration per size class
     bool tma = false;              // update rows move by TMA where A allows it (measured slower)
-    int64_t gemm_min_k = 4096;     // gf2_mul: inner dimensions from here on go through the library GEMM
+    int64_t gemm_min_k = 1024;     // gf2_mul: inner dimensions from here on go through the GEMM
     int gemm_fmt = 0;              // 0: own tcgen05 FP4 GEMM; library GEMM (if built in): 4 = FP4 E2M1, 8 = FP8 E4M3
     int64_t rref_block = -1;       // RREF recovery: base block width of the recursive form (0: flat, -1: auto)
     bool wide_update = true;       // table updates on aligned rows: 128-byte tiles, nine tables
     bool naive_update = false;     // plain baseline: trailing updates as one-by-one row additions
     bool pdl = true;               // launches with programmatic dependent launch (GF2_OPT_PDL)
     int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
+    bool ple_recursive = false;    // blocked PLE by recursive halving (Algorithm 3) instead of iterated blocks
     char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
     size_t lbuf_cap = 0;
     char *tbuf = nullptr;          // blocked PLE: indices of the fused TRSM leaf
@@ -423,14 +424,63 @@ static int trsm_lower(gf2_handle *h, uint64_t *A, int64_t ld, int64_t row0, int6
     return GF2_OK;
 }
 
-// Enqueue the block-iterative PLE of A (m x ncols, pivots among the first
-// npiv columns); the rank is left in r_dev.  With a PLE block width set
-// (GF2_OPT_PLE_BLOCK), the stripes are decomposed block by block with their
-// updates restricted to the block, and the columns right of each block get
-// the block's whole trailing update at once: the TRSM U = L11^-1 A12 on the
-// block's pivot rows (one 64 x 64 diagonal inverse plus one table pass per
-// 64 pivots) and A22 ^= L21 U through gf2_mul (the FP4 GEMM for large
-// blocks).  The host reads the rank once per block.
+// The trailing update of a finished column block: the block's stripes
+// [s0, s1) took the pivot rows [r0, r1); the words [w_lo, w_hi) right of it
+// (columns up to ncols_hi) get the block's row moves, U = L11^-1 A12 on the
+// pivot rows and A22 ^= L21 U below them (Algorithm 3's TRSM and product).
+static int block_trailing(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t s0, int64_t s1,
+                          int64_t r0, int64_t r1, int64_t w_lo, int64_t w_hi, int64_t ncols_hi)
+{
+    const int64_t W = words_for(ncols);
+    {
+        Timed t(h, K_OTHER);
+        CK(launch_permute_trailing(h->stream, A, ld,
+                                   reinterpret_cast<StripeDesc *>(h->ws + layout_for(m, ncols).descs), (int)s0,
+                                   (int)s1, w_lo, w_hi));
+    }
+    h->launches += 1;
+    const int64_t kb = r1 - r0;
+    if (kb <= 0 || w_lo >= w_hi) return GF2_OK;
+    // the block's L bits, rows r0 .. m, aligned
+    const int64_t kw = words_for(kb);
+    int rc = grow(&h->lbuf, &h->lbuf_cap, (size_t)(m - r0) * kw * 8, h->stream);
+    if (rc) return rc;
+    uint64_t *Lt = reinterpret_cast<uint64_t *>(h->lbuf);
+    {
+        Timed t(h, K_OTHER);
+        CK(launch_gather_lbits(h->stream, A, ld, W, r0, m - r0, r0, kb, kw, Lt, h->num_sms));
+    }
+    h->launches += 1;
+    // U = L11^-1 A[r0:r1, w_lo:w_hi)
+    if ((rc = trsm_lower(h, A, ld, r0, kb, Lt, kw, w_lo, w_hi, ncols_hi))) return rc;
+    // A[r1:m, w_lo:w_hi) ^= L21 U
+    if (r1 < m) {
+        rc = gf2_mul(h, A + r1 * ld + w_lo, ld, Lt + kb * kw, kw, A + r0 * ld + w_lo, ld, m - r1, kb,
+                     ncols_hi - 64 * w_lo, 1);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+static int read_rank(gf2_handle *h, int64_t *r)
+{
+    CK(cudaMemcpyAsync(r, r_dev(h), sizeof(*r), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GF2_OK;
+}
+
+// Enqueue the PLE of A (m x ncols, pivots among the first npiv columns); the
+// rank is left in r_dev.  Three forms:
+//  - per stripe (no block width): Algorithm 2's loop over all stripes, each
+//    stripe's update over the whole row;
+//  - iterated blocks (GF2_OPT_PLE_BLOCK, the default from 65536 pivot
+//    columns): the stripes are decomposed block by block with their updates
+//    restricted to the block, and the columns right of each block get the
+//    block's whole trailing update at once (block_trailing);
+//  - recursive (GF2_OPT_PLE_RECURSIVE): Algorithm 3, the columns halved until
+//    a half is no wider than the block width, each left half's trailing
+//    update applied to its right sibling's columns only.
+// The host reads the rank once per block.
 int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv, int64_t *P,
             int64_t *Q)
 {
@@ -441,6 +491,24 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     // per stripe; at 32768^2 blocking does not pay)
     const int64_t bs = h->ple_block >= 0 ? h->ple_block / 64 : (npiv >= 65536 ? 256 : 0);
     if (bs <= 0 || ns <= bs) return run_ple_range(h, A, m, ncols, ld, npiv, P, Q, 0, ns, W, true);
+    if (h->ple_recursive) {
+        // rec(a, b, w_hi): the stripes [a, b), whose updates reach the word
+        // w_hi (W at the root; the right sibling's end below it)
+        std::function<int(int64_t, int64_t, int64_t)> rec = [&](int64_t a, int64_t b, int64_t w_hi) -> int {
+            const bool last = w_hi == W;
+            if (b - a <= bs) return run_ple_range(h, A, m, ncols, ld, npiv, P, Q, a, b, w_hi, a == 0, last);
+            const int64_t mid = a + (b - a + 1) / 2;
+            int64_t r0 = 0, r1 = 0;
+            int rc;
+            if (a > 0 && (rc = read_rank(h, &r0))) return rc;
+            if ((rc = rec(a, mid, mid))) return rc;
+            if ((rc = read_rank(h, &r1))) return rc;
+            rc = block_trailing(h, A, m, ncols, ld, a, mid, r0, r1, mid, w_hi, std::min(ncols, 64 * w_hi));
+            if (rc) return rc;
+            return rec(mid, b, w_hi);
+        };
+        return rec(0, ns, W);
+    }
     int64_t r0 = 0;
     for (int64_t s0 = 0; s0 < ns; s0 += bs) {
         const int64_t s1 = std::min(ns, s0 + bs);
@@ -449,37 +517,10 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
         int rc = run_ple_range(h, A, m, ncols, ld, npiv, P, Q, s0, s1, W_upd, s0 == 0, last);
         if (rc) return rc;
         if (last) break;
-        // the block's row moves, applied to the words right of it at once
-        {
-            Timed t(h, K_OTHER);
-            CK(launch_permute_trailing(h->stream, A, ld, reinterpret_cast<StripeDesc *>(h->ws + layout_for(m, ncols).descs),
-                                       (int)s0, (int)s1, W_upd, W));
-        }
-        h->launches += 1;
         int64_t r1 = 0;
-        CK(cudaMemcpyAsync(&r1, r_dev(h), sizeof(r1), cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        const int64_t kb = r1 - r0;
-        if (kb > 0) {
-            // the block's L bits, rows r0 .. m, aligned
-            const int64_t kw = words_for(kb);
-            rc = grow(&h->lbuf, &h->lbuf_cap, (size_t)(m - r0) * kw * 8, h->stream);
-            if (rc) return rc;
-            uint64_t *Lt = reinterpret_cast<uint64_t *>(h->lbuf);
-            {
-                Timed t(h, K_OTHER);
-                CK(launch_gather_lbits(h->stream, A, ld, W, r0, m - r0, r0, kb, kw, Lt, h->num_sms));
-            }
-            h->launches += 1;
-            // U = L11^-1 A[r0:r1, W_upd:W]
-            if ((rc = trsm_lower(h, A, ld, r0, kb, Lt, kw, W_upd, W, ncols))) return rc;
-            // A[r1:m, W_upd:W] ^= L21 U
-            if (r1 < m) {
-                rc = gf2_mul(h, A + r1 * ld + W_upd, ld, Lt + kb * kw, kw, A + r0 * ld + W_upd, ld, m - r1, kb,
-                             ncols - 64 * W_upd, 1);
-                if (rc) return rc;
-            }
-        }
+        if ((rc = read_rank(h, &r1))) return rc;
+        rc = block_trailing(h, A, m, ncols, ld, s0, s1, r0, r1, W_upd, W, ncols);
+        if (rc) return rc;
         r0 = r1;                                         // later blocks still run: their stripe records
     }                                                    // (rank 0 once no row is left) feed the RREF
     return GF2_OK;
@@ -1620,6 +1661,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
     case GF2_OPT_WIDE_UPDATE: h->wide_update = value != 0; return GF2_OK;
     case GF2_OPT_NAIVE_UPDATE: h->naive_update = value != 0; return GF2_OK;
     case GF2_OPT_PDL: h->pdl = value != 0; return GF2_OK;
+    case GF2_OPT_PLE_RECURSIVE: h->ple_recursive = value != 0; return GF2_OK;
     case GF2_OPT_MUL_GEMM_FORMAT:
         if (value != 8 && value != 4 && value != 0) return GF2_EINVAL;
         if (value != 0 && !kLibraryGemm) return GF2_EINVAL;   // library GEMM not built in

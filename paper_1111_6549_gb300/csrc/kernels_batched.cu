@@ -124,7 +124,8 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
 {
     extern __shared__ __align__(16) uint64_t T[];    // BTAB_WORDS: [table][entry][tile word]
     __shared__ PanelShared sh;
-    __shared__ uint64_t sLinv[KS];
+    __shared__ uint64_t sLinv[KS], sMinv[KS], sBx[KS];
+    __shared__ int8_t sCol[KS];
     __shared__ int16_t smap[BATCH_MAX_ROWS];          // position offset -> staged slot, or -1
     __shared__ int sh_item;
     __shared__ __align__(16) uint64_t sG[BG_WORDS];   // generator words of the current tile
@@ -166,7 +167,10 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
             __syncthreads();
             const int rbar = sh.rbar;
             if (rbar == 0) continue;
+            // L11^-1 and U11^-1 side by side (the window's register budget
+            // here leaves no room to form them during the search)
             if (warp == 0) warp_lower_inverse_blocked(sh.L, rbar, sLinv);
+            if (warp == 1) warp_upper_inverse(sh, rbar, T, T + KS, sMinv);   // scratch in T (free here)
             for (int p = tid; p < rbar; p += BATCH_THREADS) {
                 it.P[r + p] = r + sh.t[p];
                 it.Q[r + p] = c + sh.j[p];
@@ -177,6 +181,33 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
             for (int64_t t = tid; t < (int64_t)nS * W; t += BATCH_THREADS) {
                 const int64_t k = t / W, w = t - k * W;
                 S[k * ldS + w] = A[sh.Ssrc[k] * ld + w];
+            }
+            // the bases of the row lookups: for a stripe word with bits u on
+            // the pivot columns, its L coefficients v = u U11^-1 and its table
+            // index v L11^-1 are XORs over the set bits of u of one row per
+            // pivot p: row p of U11^-1 and of U11^-1 L11^-1
+            if (tid < KS) sCol[tid] = -1;
+            __syncthreads();
+            if (tid < rbar) {
+                const uint64_t mp = sMinv[tid];
+                uint64_t x = 0;
+                for (int q = 0; q < rbar; ++q) x ^= sLinv[q] & (0ull - ((mp >> q) & 1ull));
+                sBx[tid] = x;
+                sCol[sh.j[tid]] = (int8_t)tid;
+            }
+            // the lookup tables in T (free until the update), built level by
+            // level: entry e of a byte's table is entry e - 2^l plus the basis
+            // row of bit l, for 2^l <= e < 2^(l+1); [kind * 8 + byte][256]
+            if (tid < 16) T[tid * 256] = 0ull;
+            for (int l = 0; l < 8; ++l) {
+                __syncthreads();
+                const int cnt = 1 << l;
+                for (int e2 = tid; e2 < 16 * cnt; e2 += BATCH_THREADS) {
+                    const int tb = e2 >> l, e = cnt + (e2 & (cnt - 1));
+                    const int p = sCol[8 * (tb & 7) + l];
+                    const uint64_t basis = p < 0 ? 0ull : (tb >= 8 ? sBx[p] : sMinv[p]);
+                    T[tb * 256 + e] = T[tb * 256 + e - cnt] ^ basis;
+                }
             }
             __syncthreads();
             // every row at a position >= r: L bits in place (staged rows: in S)
@@ -190,14 +221,14 @@ batched_ple_kernel(const gf2_batch_item *items, const int32_t *order, int count,
                     es = sh.E[k];
                     ix = sLinv[k] ^ (1ull << k);
                 } else {
-                    uint64_t sw = row[cw];
+                    const uint64_t sw = row[cw];
                     v = 0;
-                    for (int p = 0; p < rbar; ++p) {
-                        const uint64_t bit = (sw >> sh.j[p]) & 1ull;
-                        sw ^= sh.E[p] & (0ull - bit);
-                        v |= bit << p;
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        const int e = (int)((sw >> (8 * b)) & 255ull);
+                        v ^= T[b * 256 + e];
+                        ix ^= T[(8 + b) * 256 + e];
                     }
-                    for (int p = 0; p < rbar; ++p) ix ^= sLinv[p] & (0ull - ((v >> p) & 1ull));
                 }
                 batch_write_lregion(row, r, cw, rbar, v, es);
                 idx[off] = ix;
@@ -269,6 +300,8 @@ cudaError_t launch_batched(cudaStream_t st, const gf2_batch_item *items, const i
     scr.gsrc = reinterpret_cast<int32_t *>(scr.glb + per_idx * grid);
     uint32_t tune_bits = 0;                           // 4 bits per size class
     for (int c = 0; c < BATCH_CLASSES; ++c) tune_bits |= (uint32_t)(tune.cfg[c] & 15) << (4 * c);
+    // (the dynamic shared-memory limit was raised by batched_grid, which
+    // every caller runs first, outside any stream capture)
     batched_ple_kernel<<<grid, BATCH_THREADS, batched_smem_bytes(), st>>>(items, order, count, next, scr,
                                                                           tune_bits);
     return cudaGetLastError();
@@ -284,7 +317,9 @@ size_t batched_scratch_words(int64_t max_rows, int64_t ldS, int grid)
 int batched_grid(int num_sms)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_ple_kernel, BATCH_THREADS,
+    if (cudaFuncSetAttribute(batched_ple_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batched_smem_bytes()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_ple_kernel, BATCH_THREADS,
                                                       batched_smem_bytes()) != cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;

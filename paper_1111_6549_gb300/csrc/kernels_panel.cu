@@ -101,31 +101,11 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
     const int rbar = sh.rbar;
     __shared__ uint64_t sMinv[KS], sLinv[KS];          // shared copies for the prep tables
     if (warp == 1) {
-        // U11^-1 for the RREF recovery, U11[p][q] = E11[p] at column qbar[q]
-        // (unit upper triangular): reversing the order of rows and columns
-        // makes it unit lower triangular, inverted in 32 x 32 blocks beside
-        // warp 0's L11^-1
+        // U11^-1 for the RREF recovery, beside warp 0's L11^-1
         __shared__ uint64_t sU[KS], sUi[KS];
-        for (int p = lane; p < KS; p += 32) {
-            uint64_t u = 0;
-            if (p < rbar) {
-                const uint64_t e = sh.E[p];
-#pragma unroll 16
-                for (int q = 0; q < KS; ++q)
-                    u |= (q < rbar ? ((e >> (sh.j[q] & 63)) & 1ull) : 0ull) << q;
-            } else {
-                u = 1ull << p;
-            }
-            sU[63 - p] = __brevll(u);                       // row 63 - p of the reversed matrix
-        }
+        warp_upper_inverse(sh, rbar, sU, sUi, sMinv);
         __syncwarp();
-        warp_lower_inverse_blocked(sU, KS, sUi);
-        __syncwarp();
-        for (int p = lane; p < rbar; p += 32) {
-            const uint64_t v = __brevll(sUi[63 - p]);
-            d->Minv[p] = v;
-            sMinv[p] = v;
-        }
+        for (int p = lane; p < rbar; p += 32) d->Minv[p] = sMinv[p];
     }
     if (warp == 0) warp_lower_inverse_blocked(sh.L, rbar, d->Linv, sLinv);
     for (int p = tid; p < rbar; p += blockDim.x) {

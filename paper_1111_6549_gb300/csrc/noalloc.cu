@@ -109,21 +109,23 @@ extern "C" int gf2_ple_noalloc(uint64_t *A, int64_t m, int64_t n, int64_t ld_wor
     *rank = 0;
     if (m == 0) return GF2_OK;
 
+    // the call synchronises the stream between launches: it cannot be
+    // captured (checked first: no other runtime call happens on a stream that
+    // is capturing)
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NA_CK(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return GF2_EINVAL;
     int dev = 0;
     NA_CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NA_MAX_DEVICES) return GF2_EINVAL;
     NoallocDevice *nd = nullptr;
     int rc = noalloc_setup(dev, &nd);
     if (rc) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the scratch address is the current device's: the work must run there
     int sdev = dev;
     NA_CK(cudaStreamGetDevice(st, &sdev));
     if (sdev != dev) return GF2_EINVAL;
-    // the call synchronises the stream between launches: it cannot be captured
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    NA_CK(cudaStreamIsCapturing(st, &cap));
-    if (cap != cudaStreamCaptureStatusNone) return GF2_EINVAL;
 
     char *base = nd->base;
     int64_t *r_dev = reinterpret_cast<int64_t *>(base + OFF_SMALL);

@@ -467,4 +467,29 @@ __device__ __forceinline__ void warp_lower_inverse_blocked(const uint64_t *Lrows
     }
 }
 
+// U11^-1 by one warp from the pivot rows of a finished search: U11[p][q] is
+// bit qbar[q] of E[p] (unit upper triangular); reversing the order of rows
+// and columns makes it unit lower triangular, inverted in 32 x 32 blocks.
+// sU, sUi: 64-word scratch.  Writes row p of U11^-1 to out[p] for p < rbar.
+__device__ __forceinline__ void warp_upper_inverse(const PanelShared &sh, int rbar, uint64_t *sU, uint64_t *sUi,
+                                                   uint64_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p = lane; p < KS; p += 32) {
+        uint64_t u = 0;
+        if (p < rbar) {
+            const uint64_t e = sh.E[p];
+#pragma unroll 16
+            for (int q = 0; q < KS; ++q) u |= (q < rbar ? ((e >> (sh.j[q] & 63)) & 1ull) : 0ull) << q;
+        } else {
+            u = 1ull << p;
+        }
+        sU[63 - p] = __brevll(u);                       // row 63 - p of the reversed matrix
+    }
+    __syncwarp();
+    warp_lower_inverse_blocked(sU, KS, sUi);
+    __syncwarp();
+    for (int p = lane; p < rbar; p += 32) out[p] = __brevll(sUi[63 - p]);
+}
+
 }  // namespace gf2

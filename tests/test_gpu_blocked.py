@@ -113,3 +113,41 @@ def test_blocked_rref_pivot_gaps(dups, rref_block):
     assert r == r0 and np.array_equal(Q.cpu().numpy()[:r0], Q0[:r0])
     assert not set(dups) & set(Q0[:r0].tolist())
     assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+
+
+@pytest.mark.parametrize("block", [64, 192, 256])
+@pytest.mark.parametrize("kind,m,n", [("dense", 1000, 1500), ("lowrank", 700, 900), ("lastrow_pivot", 600, 800),
+                                      ("zerocols", 800, 1000), ("dense", 1500, 700), ("duprows", 640, 640)])
+def test_recursive_ple_matches_oracle(block, kind, m, n):
+    """Algorithm 3's recursion (GF2_OPT_PLE_RECURSIVE): columns halved down to
+    the block width, each left half's trailing update on its sibling only."""
+    import paper_1111_6549_gb300 as g
+    h = handle(block)
+    h.set_option(g.OPT_PLE_RECURSIVE, 1)
+    A = make(kind, m, n, seed=block + 7 * m)
+    assert_ple_equal(run(h, A, m, n, ld_extra=1), ref_ple(A, m, n))
+
+
+def test_recursive_ple_rref_and_solve():
+    """The RREF and the solve on top of the recursive PLE."""
+    import paper_1111_6549_gb300 as g
+    h = handle(128, 1)
+    h.set_option(g.OPT_PLE_RECURSIVE, 1)
+    m, n = 1800, 2100
+    A = make("lowrank", m, n, seed=21)
+    dR = to_dev(A)
+    Q = vec_dev(min(m, n))
+    r = h.rref(dR, m, n, Q)
+    R0 = A.copy()
+    r0, Q0 = oracle.rref(R0, m, n)
+    assert r == r0 and np.array_equal(to_host(dR, gi.words_for(n)), R0)
+    nn, nrhs = 1300, 33
+    As = make("dense", nn, nn, seed=22)
+    Bs = gi.bernoulli_matrix(nn, nrhs, 23)
+    dA, dB = to_dev(As), to_dev(Bs)
+    st = h.solve(dA, dB, nn, nrhs)
+    A0, B0 = As.copy(), Bs.copy()
+    st0, _ = oracle.solve(A0, B0, nn, nrhs)
+    assert st == st0
+    if st0 != oracle.SOLVE_INCONSISTENT:
+        assert np.array_equal(to_host(dB, gi.words_for(nrhs)), B0)
