@@ -163,7 +163,7 @@ struct UpdArgs {
     const StripeDesc *snap_desc;
     uint64_t *idx_next;
     int64_t skip_lo, skip_hi;  // words [skip_lo, skip_hi) may be left out (zero in every row
-                               // involved); only the pipelined table kernel uses it
+                               // involved); the pipelined table kernels use it
 };
 
 // A CUtensorMap (128 bytes) kept opaque outside the files that use TMA.
@@ -197,6 +197,9 @@ cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int
 cudaError_t setup_update_kernel();
 cudaError_t setup_prep_kernel();
 cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms);
+// the fused RREF stripe pass (UpdArgs::rref_fused; kernels_rref_pass.cu)
+cudaError_t setup_rref_pass_kernel();
+cudaError_t launch_rref_pass(cudaStream_t st, const UpdArgs &a, int num_sms);
 bool update_vectorised(const UpdArgs &a);   // true when the paired, pipelined form runs
 cudaError_t launch_update_tc(cudaStream_t st, const UpdArgs &a, int num_sms);
 cudaError_t launch_tc_mul(cudaStream_t st, uint64_t *C, int64_t ldc, const uint64_t *A, int64_t lda, const uint64_t *B,

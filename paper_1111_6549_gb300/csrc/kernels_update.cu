@@ -223,33 +223,6 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_kernel(UpdArgs a)
 // still selects generator row j.  The eight lanes of a row read one whole
 // 128-byte entry per lookup, so lookups are conflict-free; CTAs take whole
 // lines and need no partner.
-// The fused RREF pass's bookends (grid-stride over the whole grid): the
-// previous pass's reduced pivot rows from gbuf_r into A, and the next
-// pass's table index.  Neither touches a word this pass reads or writes:
-// the previous stripe's pivot rows lie below this stripe's rows, and the
-// next stripe's word lies left of this pass's words.
-__device__ __forceinline__ void rref_side_jobs(const UpdArgs &a, int64_t W)
-{
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
-    if (a.flush_desc) {
-        const StripeDesc *f = a.flush_desc;
-        const int rbar = f->rbar;
-        const int64_t c0 = f->c >> 6;
-        const int64_t nw = W - c0;
-        if (rbar > 0 && nw > 0)
-            for (int64_t e = gt; e < rbar * nw; e += gs) {
-                const int64_t t = e / nw, word = c0 + (e - t * nw);
-                if (word >= a.skip_lo && word < a.skip_hi) continue;
-                a.A[(f->r + t) * a.ld + word] = a.gbuf_r[t * a.ldg + word];
-            }
-    }
-    if (a.snap_desc) {
-        const StripeDesc *sd = a.snap_desc;
-        const int64_t cw = sd->c >> 6;
-        for (int64_t i = a.row_lo + gt; i < sd->r; i += gs) a.idx_next[i] = a.A[i * a.ld + cw];
-    }
-}
-
 constexpr int PIPE_RPT = 4;
 
 struct RowBatch {
@@ -257,26 +230,17 @@ struct RowBatch {
     int64_t ri[PIPE_RPT];
 };
 
-// The body of the pipelined table kernels; FUSED: the RREF pass with the
-// block reduction fused in (rref_pass_kernel, wide tiles only).
-template <bool WIDE, bool FUSED>
+// The body of the pipelined table kernels.
+template <bool WIDE>
 __device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
 {
     __shared__ const uint64_t *sGen[KS];
-    // fused RREF passes: the stripe's raw pivot rows and its reduced rows by
-    // pivot column, one tile wide; U11^-1
-    __shared__ __align__(16) uint64_t sRaw[FUSED ? KS * WT : 1], sGc[FUSED ? KS * WT : 1];
-    __shared__ uint64_t sMinv[FUSED ? KS : 1];
-    __shared__ int8_t sCol[FUSED ? KS : 1];
 
     int64_t row_lo, row_hi, w_lo;
     const int64_t W = a.W;
     int64_t r = 0;
     int maxpos = -1, nS = 0, rbar_m = 0;
     const StripeDesc *d = a.desc;
-    constexpr bool fused = FUSED;
-    static_assert(!FUSED || WIDE, "the fused RREF pass uses wide tiles");
-    if (fused) rref_side_jobs(a, W);
     if (a.mode == UPD_PLE) {
         const int rbar = d->rbar;
         if (rbar == 0) return;
@@ -297,10 +261,6 @@ __device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
         if (threadIdx.x < KS) sGen[threadIdx.x] = nullptr;
         __syncthreads();
         if (threadIdx.x < rbar) sGen[d->qbar[threadIdx.x]] = a.A + (d->r + threadIdx.x) * a.ld;
-        if (fused && threadIdx.x < KS) {
-            sMinv[threadIdx.x] = threadIdx.x < rbar ? d->Minv[threadIdx.x] : 0ull;
-            sCol[threadIdx.x] = threadIdx.x < rbar ? (int8_t)d->qbar[threadIdx.x] : (int8_t)-1;
-        }
     } else if (a.mode == UPD_M4RI) {
         rbar_m = d->rbar;
         if (rbar_m == 0) return;
@@ -335,7 +295,7 @@ __device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
     }
 
     const int64_t R = row_hi - row_lo;
-    if (w_lo >= W || (R <= 0 && !fused)) return;
+    if (w_lo >= W || R <= 0) return;
     // The column range in units: tile pairs of 64-byte tiles (paired form),
     // 128-byte tiles (wide form); tp_lo / tp_hi select a range of units, and
     // unit 0 holds the first word w_lo either way.
@@ -351,40 +311,6 @@ __device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
     }
     const int64_t NT = n1 + (a1 - b0);
     auto phys = [&](int64_t t) -> int64_t { return t < n1 ? a0 + t : b0 + (t - n1); };
-    // fused RREF pass: G = U11^-1 (raw pivot rows) on the tile at wbase, by
-    // pivot column in sGc; the pass's words go to gbuf_w as well (written
-    // back to the pivot rows by the next pass, when no CTA reads them raw)
-    auto fused_g = [&](int64_t wbase) {
-        const int rbar = d->rbar;
-        for (int e = threadIdx.x; e < KS * WT; e += blockDim.x) {
-            const int t = e / WT, ww = e % WT;
-            const int64_t word = wbase + ww;
-            sRaw[e] = (t < rbar && word < W) ? a.A[(d->r + t) * a.ld + word] : 0ull;
-            sGc[e] = 0ull;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < KS * WT; e += blockDim.x) {
-            const int t = e / WT, ww = e % WT;
-            if (t >= rbar) continue;
-            const uint64_t mrow = sMinv[t];
-            uint64_t acc = 0;
-#pragma unroll 8
-            for (int q = 0; q < KS; ++q) acc ^= sRaw[q * WT + ww] & (0ull - ((mrow >> q) & 1ull));
-            sGc[sCol[t] * WT + ww] = acc;
-            const int64_t word = wbase + ww;
-            const bool in_skip = word >= a.skip_lo && word < a.skip_hi;
-            if (word >= w_lo && word < W && !in_skip) a.gbuf_w[t * a.ldg + word] = acc;
-        }
-        __syncthreads();
-    };
-    if (fused && R <= 0) {
-        // no rows above: only the reduced pivot rows, tiles round-robin
-        for (int64_t t = blockIdx.x; t < NT; t += gridDim.x) {
-            __syncthreads();
-            fused_g(phys(t) * TWK);
-        }
-        return;
-    }
     const int64_t NU = WIDE ? NT : (NT + 1) / 2;
     const int64_t tp_lo = min(a.tp_lo, NU);
     const int64_t tp_hi = (a.tp_hi < 0) ? NU : min(a.tp_hi, NU);
@@ -419,10 +345,7 @@ __device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
         if (tile >= NT) continue;
         const int64_t wbase = phys(tile) * TWK;
         __syncthreads();
-        if (fused) {
-            fused_g(wbase);
-            build_wide_tables_smem(T, sGc);
-        } else if (WIDE) build_wide_tables(T, sGen, wbase, W, w_lo);
+        if (WIDE) build_wide_tables(T, sGen, wbase, W, w_lo);
         else build_tables(T, sGen, wbase, W);
         __syncthreads();
 
@@ -519,21 +442,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) update_pipe_kernel(UpdArgs a)
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) uint64_t T[];
-    update_pipe_body<WIDE, false>(a, T);
+    update_pipe_body<WIDE>(a, T);
 }
-
-// One RREF stripe pass with the stripe's block reduction fused in (see
-// UpdArgs::rref_fused): the table update of the rows above the stripe, the
-// reduced pivot rows formed per tile, and the neighbouring passes' write-back
-// and index snapshot.
-__global__ void __launch_bounds__(UPD_THREADS, 1) rref_pass_kernel(UpdArgs a)
-{
-    pdl_wait();
-    pdl_trigger();
-    extern __shared__ __align__(16) uint64_t T[];
-    update_pipe_body<true, true>(a, T);
-}
-
 
 // ----------------------------------------------------------------------------
 // Naive form, the plain baseline: no tables.  One thread per (row, word) adds
@@ -620,8 +530,7 @@ cudaError_t setup_update_kernel()
     e = cudaFuncSetAttribute(update_pipe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(WIDE_TAB_WORDS * sizeof(uint64_t)));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(rref_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(WIDE_TAB_WORDS * sizeof(uint64_t)));
+    e = setup_rref_pass_kernel();
     if (e != cudaSuccess) return e;
     e = setup_update_tma_kernel();
     if (e != cudaSuccess) return e;
@@ -651,11 +560,7 @@ cudaError_t launch_update(cudaStream_t st, const UpdArgs &a, int num_sms)
         if (grid < 2) grid = 2;
         if (a.tmap)
             return launch_update_tma(st, a, grid);
-        if (a.rref_fused && a.wide) {
-            int gw = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
-            return launch_kernel(rref_pass_kernel, dim3(gw), dim3(UPD_THREADS), WIDE_TAB_WORDS * sizeof(uint64_t), st,
-                                 a);
-        }
+        if (a.rref_fused && a.wide) return launch_rref_pass(st, a, num_sms);   // kernels_rref_pass.cu
         if (a.wide) {
             int gw = (a.grid > 0 && a.grid < num_sms) ? a.grid : num_sms;
             return launch_kernel(update_pipe_kernel<true>, dim3(gw), dim3(UPD_THREADS),
