@@ -614,8 +614,8 @@ def tc_compare(args):
     # form on operands already in place (AND-population counts per second;
     # each launch's count is checked against the exact value)
     out["carriers"] = {}
-    for name, c, per in (("fp4_tcgen05_mxf4", g.CARRIER_FP4, 64), ("fp8_tcgen05_f8f6f4", g.CARRIER_FP8, 64),
-                         ("b1_mma_sync_and_popc", g.CARRIER_B1, 256)):
+    for name, c, per in (("fp4_tcgen05_mxf4", g.CARRIER_FP4, 64), ("fp4_tcgen05_mxf4nvf4_4x", g.CARRIER_NVF4, 64),
+                         ("fp8_tcgen05_f8f6f4", g.CARRIER_FP8, 64), ("b1_mma_sync_and_popc", g.CARRIER_B1, 256)):
         t0 = time.time()
         g.carrier_rate(c, 1024)
         est_ms = (time.time() - t0) * 1e3 / 1024

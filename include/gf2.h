@@ -428,12 +428,14 @@ int gf2_get_timeline(gf2_handle_t handle, double *out, int64_t max_records, int6
 /*
  * Tensor-core carriers of a GF(2) product (Section 3.3: the block step of
  * Algorithm 3 is a matrix multiplication; over GF(2) it is an integer
- * product of 0/1 matrices reduced mod 2).  Three carriers run on sm_103a:
+ * product of 0/1 matrices reduced mod 2).  Four carriers run on sm_103a:
  *   GF2_CARRIER_B1   warp-level mma.sync m16n8k256 on 1-bit operands, AND and
  *                    population count into int32 counts;
  *   GF2_CARRIER_FP8  tcgen05.mma kind::f8f6f4 on E4M3 0/1 (M128 N256 K32);
  *   GF2_CARRIER_FP4  tcgen05.mma kind::mxf4 block-scaled, E2M1 0/1 packed two
- *                    per byte, scales 2^0 (M128 N256 K64).
+ *                    per byte, UE8M0 scales 2^0 per 32 elements (M128 N256 K64);
+ *   GF2_CARRIER_NVF4 tcgen05.mma kind::mxf4nvf4 with scale_vec::4X, the same
+ *                    operands with UE4M3 scales 1.0 per 16 elements.
  * (The integer tensor-core form kind::i8 is not accepted for sm_103a.)
  * Both calls use the current device and its default stream, allocate a few
  * bytes of device memory and synchronise the device.
@@ -442,11 +444,11 @@ int gf2_get_timeline(gf2_handle_t handle, double *out, int64_t max_records, int6
  *   B1:       a_bits 16 rows x 4 words (256 bits), b_bits 8 columns x 4
  *             words; counts int32[16 x 8], counts[i * 8 + j] = popcount of
  *             (row i AND column j).
- *   FP8, FP4: a_bits 128 rows x 1 word, b_bits 256 columns x 1 word; counts
+ *   FP8, FP4, NVF4: a_bits 128 rows x 1 word, b_bits 256 columns x 1 word; counts
  *             int32[128 x 256], counts[i * 256 + j] = popcount(a[i] & b[j]).
  * gf2_carrier_rate: `iters` instruction steps per warp (B1: four independent
  *   m16n8k256 per step, 8 warps per CTA, 4 CTAs per SM) or per CTA (FP8: two
- *   K32 MMAs, FP4: one K64 MMA per step, one CTA per SM) on all-ones
+ *   K32 MMAs, FP4 / NVF4: one K64 MMA per step, one CTA per SM) on all-ones
  *   operands held in registers or shared memory; *macs_per_s = multiply-adds
  *   per second over the whole GPU, *count_out (may be NULL) = one final
  *   count (iters * 256 for B1, iters * 64 otherwise).  GF2_EINVAL when a
@@ -457,6 +459,7 @@ int gf2_get_timeline(gf2_handle_t handle, double *out, int64_t max_records, int6
 #define GF2_CARRIER_B1  1
 #define GF2_CARRIER_FP4 4
 #define GF2_CARRIER_FP8 8
+#define GF2_CARRIER_NVF4 16
 int gf2_carrier_check(int carrier, const uint64_t *a_bits, const uint64_t *b_bits, int32_t *counts);
 int gf2_carrier_rate(int carrier, int64_t iters, double *macs_per_s, int64_t *count_out);
 

@@ -29,7 +29,7 @@ GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6
  OPT_PLE_RECURSIVE) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
 BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
-CARRIER_B1, CARRIER_FP4, CARRIER_FP8 = 1, 4, 8
+CARRIER_B1, CARRIER_FP4, CARRIER_FP8, CARRIER_NVF4 = 1, 4, 8, 16
 
 
 class GF2Error(RuntimeError):

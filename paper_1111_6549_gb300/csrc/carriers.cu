@@ -8,8 +8,10 @@
 //   b1    mma.sync m16n8k256 .b1 AND + POPC (int32 counts), the legacy warp
 //         path;
 //   fp8   tcgen05.mma kind::f8f6f4, E4M3 1.0 = 0x38, fp32 counts;
-//   fp4   tcgen05.mma kind::mxf4 with block scales (UE8M0, all 2^0), E2M1
-//         1.0 = 0x2 packed two per byte, fp32 counts.
+//   fp4   tcgen05.mma kind::mxf4 with block scales (UE8M0, all 2^0, one per
+//         32 elements), E2M1 1.0 = 0x2 packed two per byte, fp32 counts;
+//   nvf4  tcgen05.mma kind::mxf4nvf4, the same E2M1 operands with UE4M3
+//         scales (all 1.0 = 0x38) one per 16 elements (scale_vec::4X).
 // (kind::i8 is not accepted for sm_103a by this toolkit's assembler.)
 // gf2_carrier_rate() runs one kernel of each carrier on every SM with the
 // operands resident (registers or shared memory) and reports multiply-adds
@@ -38,6 +40,8 @@ constexpr uint32_t IDESC_F8 = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 
 // E2M1 (1 at bits 7-9 and 10-12), K-major, N >> 3 at bit 17, scale type
 // UE8M0 (bit 23), M >> 4 at bit 24 (M = 128), K = 64.
 constexpr uint32_t IDESC_F4 = (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | (1u << 23) | ((128u >> 4) << 24);
+// kind::mxf4nvf4 with scale_vec::4X: as above with scale type UE4M3 (bit 23 = 0).
+constexpr uint32_t IDESC_NVF4 = (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t cr_saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -87,6 +91,15 @@ __device__ __forceinline__ void cr_mma_f4(uint32_t d, uint64_t a, uint64_t b, ui
         "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
         " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(IDESC_F4), "r"(sfa), "r"(sfb), "r"(acc));
+}
+
+__device__ __forceinline__ void cr_mma_nvf4(uint32_t d, uint64_t a, uint64_t b, uint32_t sfa, uint32_t sfb,
+                                            uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::mxf4nvf4.block_scale.scale_vec::4X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC_NVF4), "r"(sfa), "r"(sfb), "r"(acc));
 }
 
 __device__ __forceinline__ void cr_commit(uint64_t *bar)
@@ -188,8 +201,9 @@ __global__ void __launch_bounds__(CR_THREADS, 1) carrier_tc_kernel(CrArgs a)
     __syncthreads();
     cr_fence_after();
     const uint32_t tmem = tmem_base;
-    // block scales: 2^0 (UE8M0 0x7F) in every byte of 32 columns, all lanes
+    // block scales 1.0 in every byte of 32 columns, all lanes: UE8M0 0x7F, UE4M3 0x38
     if (carrier == GF2_CARRIER_FP4) cr_st32(tmem + ((uint32_t)(32 * warp) << 16) + CR_SCALE_COL, 0x7F7F7F7Fu);
+    if (carrier == GF2_CARRIER_NVF4) cr_st32(tmem + ((uint32_t)(32 * warp) << 16) + CR_SCALE_COL, 0x38383838u);
     cr_fence_before();
     __syncthreads();
     cr_fence_after();
@@ -204,9 +218,11 @@ __global__ void __launch_bounds__(CR_THREADS, 1) carrier_tc_kernel(CrArgs a)
                 // two K = 32 steps over the 64-byte rows (4 groups per row)
                 cr_mma_f8(tmem, cr_desc(a0, 128, 512), cr_desc(b0, 128, 512), i > 0 ? 1u : 0u);
                 cr_mma_f8(tmem, cr_desc(a0 + 256, 128, 512), cr_desc(b0 + 256, 128, 512), 1u);
-            } else {
+            } else if (carrier == GF2_CARRIER_FP4) {
                 // one K = 64 step over the 32-byte rows (2 groups per row)
                 cr_mma_f4(tmem, cr_desc(a0, 128, 256), cr_desc(b0, 128, 256), sf, sf, i > 0 ? 1u : 0u);
+            } else {
+                cr_mma_nvf4(tmem, cr_desc(a0, 128, 256), cr_desc(b0, 128, 256), sf, sf, i > 0 ? 1u : 0u);
             }
         }
         cr_commit(&bar);
@@ -296,7 +312,9 @@ extern "C" {
 int gf2_carrier_check(int carrier, const uint64_t *a_bits, const uint64_t *b_bits, int32_t *counts)
 {
     if (!a_bits || !b_bits || !counts) return GF2_EINVAL;
-    if (carrier != GF2_CARRIER_B1 && carrier != GF2_CARRIER_FP8 && carrier != GF2_CARRIER_FP4) return GF2_EINVAL;
+    if (carrier != GF2_CARRIER_B1 && carrier != GF2_CARRIER_FP8 && carrier != GF2_CARRIER_FP4 &&
+        carrier != GF2_CARRIER_NVF4)
+        return GF2_EINVAL;
     int32_t *err = nullptr;
     if (cudaMalloc(reinterpret_cast<void **>(&err), sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -318,7 +336,9 @@ int gf2_carrier_check(int carrier, const uint64_t *a_bits, const uint64_t *b_bit
 int gf2_carrier_rate(int carrier, int64_t iters, double *macs_per_s, int64_t *count_out)
 {
     if (!macs_per_s || iters <= 0) return GF2_EINVAL;
-    if (carrier != GF2_CARRIER_B1 && carrier != GF2_CARRIER_FP8 && carrier != GF2_CARRIER_FP4) return GF2_EINVAL;
+    if (carrier != GF2_CARRIER_B1 && carrier != GF2_CARRIER_FP8 && carrier != GF2_CARRIER_FP4 &&
+        carrier != GF2_CARRIER_NVF4)
+        return GF2_EINVAL;
     // exact counts: every accumulator stays below 2^24 (fp32) / 2^31 (int32)
     const int64_t per = carrier == GF2_CARRIER_B1 ? 256 : 64;
     if (iters * per >= (carrier == GF2_CARRIER_B1 ? (int64_t(1) << 31) : (int64_t(1) << 24))) return GF2_EINVAL;

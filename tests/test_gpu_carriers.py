@@ -20,7 +20,8 @@ def _popc_counts(a, b, words):
     return out
 
 
-@pytest.mark.parametrize("carrier,rows,cols,words", [(1, 16, 8, 4), (8, 128, 256, 1), (4, 128, 256, 1)])
+@pytest.mark.parametrize("carrier,rows,cols,words", [(1, 16, 8, 4), (8, 128, 256, 1), (4, 128, 256, 1),
+                                                     (16, 128, 256, 1)])
 @pytest.mark.parametrize("seed", [0, 1])
 def test_carrier_counts_exact(carrier, rows, cols, words, seed):
     import torch
@@ -40,7 +41,7 @@ def test_carrier_counts_exact(carrier, rows, cols, words, seed):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("carrier,per", [(1, 256), (8, 64), (4, 64)])
+@pytest.mark.parametrize("carrier,per", [(1, 256), (8, 64), (4, 64), (16, 64)])
 def test_carrier_rate_counts(carrier, per):
     import paper_1111_6549_gb300 as g
     rate, cnt = g.carrier_rate(carrier, 64)
