@@ -131,40 +131,62 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
     // with bits u on the pivot columns, the L coefficients v = u U11^-1, the
     // table index v L11^-1 and the word rebuilt from the pivot bits
     // (u U11^-1 E11) are XORs of rows selected by u, looked up per raw byte
-    // of the word (non-pivot columns select nothing).
-    __shared__ uint64_t tMv[KS], tMx[KS], tMg[KS];
-    __shared__ int8_t tcolp[KS];
-    if (tid < KS) tcolp[tid] = -1;
+    // of the word (non-pivot columns select nothing).  The basis rows, by
+    // stripe column: row p of U11^-1, of U11^-1 L11^-1 and of U11^-1 E11 for
+    // the column's pivot p (zero for a column without one).
+    static_assert(PANEL_THREADS == 8 * KS, "eight threads per pivot for the bases");
+    __shared__ uint64_t tB[3][KS];
+    if (tid < KS) {
+        tB[0][tid] = 0ull;
+        tB[1][tid] = 0ull;
+        tB[2][tid] = 0ull;
+    }
     __syncthreads();                                   // Minv and Linv are written
-    if (tid < rbar) {
-        const uint64_t mp = sMinv[tid];
+    {
+        // pivot p's two sums over U11^-1's row, eight threads (one warp
+        // quarter) per pivot, eight terms each, folded by shuffles
+        const int p = tid >> 3, part = tid & 7;
+        const uint64_t mp = p < rbar ? sMinv[p] : 0ull;
         uint64_t x = 0, g = 0;
-        for (int q = 0; q < rbar; ++q) {
-            const uint64_t sel = 0ull - ((mp >> q) & 1ull);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int q = 8 * part + i;
+            const uint64_t sel = (q < rbar) ? 0ull - ((mp >> q) & 1ull) : 0ull;
             x ^= sLinv[q] & sel;
             g ^= sh.E[q] & sel;
         }
-        tMv[tid] = mp;
-        tMx[tid] = x;
-        tMg[tid] = g;
-        tcolp[sh.j[tid]] = (int8_t)tid;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            x ^= __shfl_xor_sync(0xffffffffu, x, o);
+            g ^= __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (part == 0 && p < rbar) {
+            const int col = sh.j[p];
+            tB[0][col] = mp;
+            tB[1][col] = x;
+            tB[2][col] = g;
+        }
     }
     __syncthreads();
-    for (int e2 = tid; e2 < 8 * 256; e2 += blockDim.x) {
-        const int b = e2 >> 8, e = e2 & 255;
-        uint64_t av = 0, ax = 0, ag = 0;
+    // thread (kind, byte b, high nibble h) writes entries 16 h .. 16 h + 15 of
+    // table (kind, b): the basis rows of the high nibble's bits XOR those of
+    // each low nibble, formed in registers
+    if (tid < 3 * 8 * 16) {
+        const int kind = tid >> 7, b = (tid >> 4) & 7, h = tid & 15;
+        const uint64_t *bs = tB[kind] + 8 * b;
+        uint64_t hv = 0;
 #pragma unroll
-        for (int bq = 0; bq < 8; ++bq) {
-            const int p = tcolp[8 * b + bq];
-            if (((e >> bq) & 1) && p >= 0) {
-                av ^= tMv[p];
-                ax ^= tMx[p];
-                ag ^= tMg[p];
-            }
+        for (int l = 0; l < 4; ++l) hv ^= ((h >> l) & 1) ? bs[4 + l] : 0ull;
+        uint64_t lo[16];
+        lo[0] = 0ull;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+#pragma unroll
+            for (int i = 0; i < (1 << l); ++i) lo[(1 << l) + i] = lo[i] ^ bs[l];
         }
-        ptab[e2] = av;
-        ptab[PREP_TAB_WORDS + e2] = ax;
-        ptab[2 * PREP_TAB_WORDS + e2] = ag;
+        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(ptab + kind * PREP_TAB_WORDS + 256 * b + 16 * h);
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) dst[i / 2] = make_ulonglong2(hv ^ lo[i], hv ^ lo[i + 1]);
     }
 }
 
