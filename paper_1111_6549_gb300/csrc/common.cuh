@@ -178,8 +178,10 @@ bool encode_row_tiles(TensorMap2D *out, const uint64_t *A, int64_t m, int64_t W,
 // ---- launchers (host side, defined in the .cu files) ----
 cudaError_t launch_init_ple(cudaStream_t st, int64_t *P, int64_t *Q, int64_t m, int64_t qn,
                             int32_t *map, int64_t *r_dev, int num_sms);
-// The panel kernel also builds the prep kernel's lookup tables (3 x 8 x 256
-// words, PREP_TAB_BYTES) in ptab when it is not null; the PLE's prep reads them.
+// The panel kernel also writes the bases of the prep kernel's lookup tables
+// (3 x 64 words by stripe column, at the start of the PREP_TAB_BYTES reserved
+// per stripe parity) to ptab when it is not null; the prep builds its tables
+// in shared memory from them.
 constexpr int PREP_TAB_WORDS = 8 * 256;
 constexpr size_t PREP_TAB_BYTES = 3 * PREP_TAB_WORDS * sizeof(uint64_t);
 // prev_map / prev_S (may be null): the previous stripe's row map and staged

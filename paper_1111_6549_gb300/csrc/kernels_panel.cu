@@ -127,13 +127,12 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         *r_dev = r + rbar;
     }
     if (ptab == nullptr) return;
-    // The prep kernel's tables (three x eight x 256 words): for a stripe word
-    // with bits u on the pivot columns, the L coefficients v = u U11^-1, the
-    // table index v L11^-1 and the word rebuilt from the pivot bits
-    // (u U11^-1 E11) are XORs of rows selected by u, looked up per raw byte
-    // of the word (non-pivot columns select nothing).  The basis rows, by
-    // stripe column: row p of U11^-1, of U11^-1 L11^-1 and of U11^-1 E11 for
-    // the column's pivot p (zero for a column without one).
+    // The bases of the prep kernel's tables: for a stripe word with bits u on
+    // the pivot columns, the L coefficients v = u U11^-1, the table index
+    // v L11^-1 and the word rebuilt from the pivot bits (u U11^-1 E11) are
+    // XORs over the word's set bits of one basis row per stripe column: row
+    // p of U11^-1, of U11^-1 L11^-1 and of U11^-1 E11 for the column's pivot
+    // p (zero for a column without one).
     static_assert(PANEL_THREADS == 8 * KS, "eight threads per pivot for the bases");
     __shared__ uint64_t tB[3][KS];
     if (tid < KS) {
@@ -168,26 +167,7 @@ panel_kernel(const uint64_t *__restrict__ A, int64_t m, int64_t ld, int64_t npiv
         }
     }
     __syncthreads();
-    // thread (kind, byte b, high nibble h) writes entries 16 h .. 16 h + 15 of
-    // table (kind, b): the basis rows of the high nibble's bits XOR those of
-    // each low nibble, formed in registers
-    if (tid < 3 * 8 * 16) {
-        const int kind = tid >> 7, b = (tid >> 4) & 7, h = tid & 15;
-        const uint64_t *bs = tB[kind] + 8 * b;
-        uint64_t hv = 0;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) hv ^= ((h >> l) & 1) ? bs[4 + l] : 0ull;
-        uint64_t lo[16];
-        lo[0] = 0ull;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-#pragma unroll
-            for (int i = 0; i < (1 << l); ++i) lo[(1 << l) + i] = lo[i] ^ bs[l];
-        }
-        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(ptab + kind * PREP_TAB_WORDS + 256 * b + 16 * h);
-#pragma unroll
-        for (int i = 0; i < 16; i += 2) dst[i / 2] = make_ulonglong2(hv ^ lo[i], hv ^ lo[i + 1]);
-    }
+    if (tid < 3 * KS) ptab[tid] = tB[tid / KS][tid % KS];   // [kind][column]: the prep builds its tables from them
 }
 
 cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t npiv, int s,
@@ -202,27 +182,39 @@ cudaError_t launch_panel(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, in
 // ----------------------------------------------------------------------------
 // prep
 
-// Write the L bits v at columns [r, r + nv) and the stripe word es at word cw
-// of one row; the old L bits below column r are kept.  Words strictly between
-// the L bits and the stripe are zero already and stay zero.
-__device__ __forceinline__ void write_lregion(uint64_t *row, int64_t r, int64_t cw, int rbar,
-                                              uint64_t v, uint64_t es)
+// The L region of one row (columns r .. r+rbar-1 get the L bits v, word cw
+// the stripe word es), from values already loaded: wkeep is the row's word
+// r/64, whose bits below column r are kept.  Words strictly between the L
+// bits and the stripe are zero already and stay zero.
+__device__ __forceinline__ void store_lregion(uint64_t *row, int64_t r, int64_t cw, int rbar, uint64_t v,
+                                              uint64_t es, uint64_t wkeep)
 {
     const int64_t wr = r >> 6;
     const int64_t wl = (r + rbar - 1) >> 6;
     for (int64_t w = wr; w <= wl; ++w) {
         const int64_t off = r - (w << 6);
         uint64_t part = (off >= 0) ? (v << off) : (v >> (-off));
-        const uint64_t keep = (w == wr) ? (row[w] & ((1ull << (r & 63)) - 1ull)) : 0ull;
+        const uint64_t keep = (w == wr) ? (wkeep & ((1ull << (r & 63)) - 1ull)) : 0ull;
         if (w == cw) part |= es;
         row[w] = keep | part;
     }
     if (cw > wl) row[cw] = es;
 }
 
-constexpr int PREP_THREADS = 256;
+// XOR over the warp's lanes (every lane gets the total).
+__device__ __forceinline__ uint64_t warp_xor(uint64_t x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x ^= __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+constexpr int PREP_THREADS = 512;
 constexpr int PREP_STAGE_BLOCKS = SMAX;   // one block per staged row
 constexpr int PREP_FIRST_ROW_BLOCK = PREP_STAGE_BLOCKS;
+constexpr int PREP_NTAB = 32;             // 3 kinds x 8 bytes of the stripe word, 8 bytes of the index
+constexpr size_t PREP_SMEM = (size_t)PREP_NTAB * 256 * sizeof(uint64_t);
+static_assert(PREP_THREADS == 16 * 32, "one warp per two tables");
 
 __global__ void __launch_bounds__(PREP_THREADS)
 prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *descs,
@@ -231,111 +223,169 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
 {
     pdl_wait();
     pdl_trigger();
-    StripeDesc *d = descs + s;
+    const StripeDesc *d = descs + s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the bases by stripe column (kind 0: L coefficients, 1: table index, 2:
+    // rebuilt word) and word nw of the raw pivot rows by pivot index (their
+    // sources, which no CTA writes here); the loads that do not depend on the
+    // stripe record go out beside it
+    __shared__ uint64_t sB[3][KS], sG[KS];
+    uint64_t b0 = 0, b1 = 0, b2 = 0;
+    int64_t src = 0;
+    if (tid < KS) {
+        b0 = ptab[tid];
+        b1 = ptab[KS + tid];
+        b2 = ptab[2 * KS + tid];
+        src = d->S_src[tid];
+    }
     const int rbar = d->rbar;
     if (rbar == 0) return;
     const int64_t r = d->r;
     const int64_t cw = d->c >> 6;
     const int nS = d->nS;
     const int maxpos = d->maxpos;
-    __shared__ uint64_t sE[KS], sLinv[KS], sG[KS];
-    for (int i = threadIdx.x; i < rbar; i += blockDim.x) {
-        sE[i] = d->E11[i];
-        sLinv[i] = d->Linv[i];
-        // word nw of the raw pivot rows (their sources, which no CTA writes here)
-        if (nw >= 0) sG[i] = A[d->S_src[i] * ld + nw];
+    if (tid < KS) {
+        sB[0][tid] = b0;
+        sB[1][tid] = b1;
+        sB[2][tid] = b2;
+        sG[tid] = (tid < rbar && nw >= 0) ? A[src * ld + nw] : 0ull;
     }
     __syncthreads();
-    // the stripe's update of word nw for a row with table index ix: the raw
-    // pivot rows selected by ix (the same sum the update kernel looks up)
-    auto next_word = [&](uint64_t ix) -> uint64_t {
-        uint64_t x = 0;
-        while (ix) {
-            const int q = __ffsll((long long)ix) - 1;
-            ix &= ix - 1;
-            x ^= sG[q];
-        }
-        return x;
-    };
+    const int64_t wr = r >> 6;                       // the word holding column r
 
     if (blockIdx.x < PREP_STAGE_BLOCKS) {
-        // staged rows: copy the whole source row, then fix its L region
+        // staged rows: copy the whole source row (keeping the words the
+        // lookups need), then fix its L region
+        __shared__ uint64_t sw3[3];                  // words cw, nw and r / 64 of the row
         for (int k = blockIdx.x; k < nS; k += PREP_STAGE_BLOCKS) {   // at most one per block
-            const uint64_t *src = A + d->S_src[k] * ld;
+            const uint64_t *srow = A + d->S_src[k] * ld;
             uint64_t *dst = S + (int64_t)k * ldS;
-            for (int64_t w = threadIdx.x; w < W; w += blockDim.x) dst[w] = src[w];
+            for (int64_t w = tid; w < W; w += blockDim.x) {
+                const uint64_t x = srow[w];
+                dst[w] = x;
+                if (w == cw) sw3[0] = x;
+                if (w == nw) sw3[1] = x;
+                if (w == wr) sw3[2] = x;
+            }
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (warp == 0) {
                 const int64_t pos = r + d->S_off[k];
+                const uint64_t sw = sw3[0];
                 uint64_t v, es, ix;
                 if (k < rbar) {
                     v = d->L11[k];
-                    es = sE[k];
-                    ix = sLinv[k] ^ (1ull << k);
+                    es = d->E11[k];
+                    ix = d->Linv[k] ^ (1ull << k);
                 } else {
-                    // a displaced row: the same table lookups as every other row
-                    const uint64_t sw = dst[cw];
+                    // a displaced row: the bases of its set bits, summed over the warp
                     uint64_t g = 0;
                     v = 0;
                     ix = 0;
 #pragma unroll
-                    for (int b = 0; b < 8; ++b) {
-                        const int e = (int)((sw >> (8 * b)) & 255ull) + 256 * b;
-                        v ^= __ldg(ptab + e);
-                        ix ^= __ldg(ptab + PREP_TAB_WORDS + e);
-                        g ^= __ldg(ptab + 2 * PREP_TAB_WORDS + e);
+                    for (int h = 0; h < 2; ++h) {
+                        const int col = lane + 32 * h;
+                        if ((sw >> col) & 1ull) {
+                            v ^= sB[0][col];
+                            ix ^= sB[1][col];
+                            g ^= sB[2][col];
+                        }
                     }
-                    if (g != sw && err) atomicExch(err, 1);
+                    v = warp_xor(v);
+                    ix = warp_xor(ix);
+                    g = warp_xor(g);
+                    if (lane == 0 && g != sw && err) atomicExch(err, 1);
                     es = 0;
                 }
-                write_lregion(dst, r, cw, rbar, v, es);
-                if (nw >= 0) dst[nw] ^= next_word(ix);
-                IDX[pos] = ix;
+                // the stripe's update of word nw: the raw pivot rows selected by ix
+                uint64_t nx = 0;
+                if (nw >= 0) {
+                    nx = (((ix >> lane) & 1ull) ? sG[lane] : 0ull) ^ (((ix >> (lane + 32)) & 1ull) ? sG[lane + 32] : 0ull);
+                    nx = warp_xor(nx);
+                }
+                if (lane == 0) {
+                    store_lregion(dst, r, cw, rbar, v, es, sw3[2]);
+                    if (nw >= 0) dst[nw] = sw3[1] ^ nx;
+                    IDX[pos] = ix;
+                }
             }
             __syncthreads();
         }
         return;
     }
-    // Every other row at a position >= r: its L coefficients v = u U11^-1
-    // (u = its bits on the pivot columns), its table index v L11^-1, and the
-    // stripe word rebuilt from u, each as eight lookups by the raw bytes of the
-    // stripe word in the tables the panel kernel built (read through L1).  A
-    // row whose word is not rebuilt exactly lies outside the span of E11: an
-    // internal error.
+    // Every other row at a position >= r: its L coefficients, its table
+    // index and its stripe word rebuilt from its pivot-column bits, each as
+    // eight lookups by the bytes of the stripe word, and the update of word
+    // nw as eight lookups by the bytes of the index.  The 32 tables are
+    // built here in shared memory, warp w forming tables 2w and 2w+1: entry
+    // 32 h + lane is the XOR of the basis rows of the low five bits (lane)
+    // and of the high three (h), so every store covers 32 consecutive words
+    // (no bank conflicts).  A row whose word is not rebuilt exactly lies
+    // outside the span of E11: an internal error.
+    extern __shared__ __align__(16) uint64_t T[];           // [kind * 8 + byte][256]
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int tb = 2 * warp + half, kind = tb >> 3, c0 = 8 * (tb & 7);
+        const uint64_t *base = kind < 3 ? sB[kind] + c0 : sG + c0;   // index byte: raw pivot rows c0 ..
+        uint64_t lo = 0;
+#pragma unroll
+        for (int l = 0; l < 5; ++l) lo ^= ((lane >> l) & 1) ? base[l] : 0ull;
+        uint64_t hv[8];
+        hv[0] = 0ull;
+        hv[1] = base[5];
+        hv[2] = base[6];
+        hv[3] = base[5] ^ base[6];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) hv[4 + h] = hv[h] ^ base[7];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) T[tb * 256 + 32 * h + lane] = hv[h] ^ lo;
+    }
+    __syncthreads();
     const int64_t stride = (int64_t)(gridDim.x - PREP_FIRST_ROW_BLOCK) * blockDim.x;
-    for (int64_t i = r + (int64_t)(blockIdx.x - PREP_FIRST_ROW_BLOCK) * blockDim.x + threadIdx.x;
-         i < m; i += stride) {
+    for (int64_t i = r + (int64_t)(blockIdx.x - PREP_FIRST_ROW_BLOCK) * blockDim.x + tid; i < m; i += stride) {
         if (i - r <= maxpos) {
             const int mv = map[i];
             if (mv >= 0 && (mv >> 8) == s) continue;       // staged row
         }
         uint64_t *row = A + i * ld;
+        // the row's words in one round trip: the stripe word, the next word,
+        // and the word holding column r (the stripe word itself at full rank)
         const uint64_t sw = row[cw];
+        const uint64_t wn = nw >= 0 ? row[nw] : 0ull;
+        const uint64_t wk = wr == cw ? sw : row[wr];
         uint64_t v = 0, ix = 0, g = 0;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            const int e = (int)((sw >> (8 * b)) & 255ull) + 256 * b;
-            v ^= __ldg(ptab + e);
-            ix ^= __ldg(ptab + PREP_TAB_WORDS + e);
-            g ^= __ldg(ptab + 2 * PREP_TAB_WORDS + e);
+            const int e = (int)((sw >> (8 * b)) & 255ull);
+            v ^= T[b * 256 + e];
+            ix ^= T[(8 + b) * 256 + e];
+            g ^= T[(16 + b) * 256 + e];
         }
         if (g != sw && err) atomicExch(err, 1);
-        write_lregion(row, r, cw, rbar, v, 0ull);
-        if (nw >= 0) row[nw] ^= next_word(ix);
+        store_lregion(row, r, cw, rbar, v, 0ull, wk);
+        if (nw >= 0) {
+            uint64_t nx = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) nx ^= T[(24 + b) * 256 + (int)((ix >> (8 * b)) & 255ull)];
+            row[nw] = wn ^ nx;
+        }
         IDX[i] = ix;
     }
 }
 
-cudaError_t setup_prep_kernel() { return cudaSuccess; }
+cudaError_t setup_prep_kernel()
+{
+    return cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PREP_SMEM);
+}
 
 cudaError_t launch_prep(cudaStream_t st, uint64_t *A, int64_t m, int64_t ld, int64_t W, int s,
                         StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS,
                         uint64_t *IDX, int32_t *err, const uint64_t *ptab, int num_sms, int64_t next_word)
 {
+    // row blocks: at most one per SM (each builds its own 64 KiB of tables)
     int64_t blocks = (m + PREP_THREADS - 1) / PREP_THREADS;
     if (blocks < 1) blocks = 1;
-    if (blocks > 4 * num_sms) blocks = 4 * num_sms;
-    return launch_kernel(prep_kernel, dim3((int)(blocks + PREP_FIRST_ROW_BLOCK)), dim3(PREP_THREADS), 0, st, A, m, ld,
+    if (blocks > num_sms) blocks = num_sms;
+    return launch_kernel(prep_kernel, dim3((int)(blocks + PREP_FIRST_ROW_BLOCK)), dim3(PREP_THREADS), PREP_SMEM, st, A, m, ld,
                          W, s, descs, map, S, ldS, IDX, err, ptab, next_word);
 }
 
