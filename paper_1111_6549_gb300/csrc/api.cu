@@ -19,6 +19,7 @@
 #include <vector>
 
 namespace gf2 {
+cudaError_t setup_trsm_leaf_kernel();   // kernels_blocked.cu: the fused leaf keeps its rows in shared memory
 thread_local bool g_pdl = false;
 }  // namespace gf2
 
@@ -840,7 +841,11 @@ int gf2_create(gf2_handle_t *handle, int device)
         delete h;
         return GF2_ECUDA;
     }
-    if (setup_update_kernel() != cudaSuccess) { cudaGetLastError(); delete h; return GF2_ECUDA; }
+    if (setup_update_kernel() != cudaSuccess || setup_trsm_leaf_kernel() != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return GF2_ECUDA;
+    }
     if (cudaMalloc(reinterpret_cast<void **>(&h->small), SM_BYTES_TOTAL) != cudaSuccess) {
         cudaGetLastError();
         delete h;

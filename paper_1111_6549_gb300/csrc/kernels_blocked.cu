@@ -152,7 +152,14 @@ trsm_leaf_prep_kernel(const uint64_t *__restrict__ Lt, int64_t ldt, int64_t kb, 
     }
 }
 
-// One CTA per pair of words; see the comment above.
+// One CTA per pair of words; see the comment above.  The CTA's two words of
+// the leaf's rows (at most TRSM_LEAF_ROWS x 16 bytes) stay in shared memory
+// for all steps: loaded once, updated in place, stored once.  Thread t owns
+// the rows t, t + 256, ... in every step, so it loads the next step's
+// indices of its rows while the current step runs.
+constexpr int LEAF_RPT = (int)(TRSM_LEAF_ROWS / LEAF_THREADS);
+constexpr size_t LEAF_SMEM = (size_t)TRSM_LEAF_ROWS * 2 * sizeof(uint64_t);
+
 __global__ void __launch_bounds__(LEAF_THREADS)
 trsm_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *__restrict__ Lp, int64_t w_lo,
                  int64_t W)
@@ -161,19 +168,40 @@ trsm_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64
     pdl_trigger();
     __shared__ __align__(16) uint64_t T[8 * 256 * 2];      // eight 8-bit tables of 16-byte entries
     __shared__ uint64_t G[KS][2];
+    extern __shared__ __align__(16) uint64_t Xs[];       // [row][2]: the CTA's two words of the leaf's rows
     const int tid = threadIdx.x;
     const int64_t w0 = w_lo + 2 * (int64_t)blockIdx.x;
     if (w0 >= W) return;
     const bool two = w0 + 1 < W;
     uint64_t *X = A + row0 * ld + w0;
+    for (int u = 0; u < LEAF_RPT; ++u) {
+        const int64_t i = tid + (int64_t)u * LEAF_THREADS;
+        if (i < kb) {
+            Xs[2 * i] = X[i * ld];
+            Xs[2 * i + 1] = two ? X[i * ld + 1] : 0ull;
+        }
+    }
     const int nsteps = (int)((kb + 63) / 64);
+    uint64_t ixn[LEAF_RPT];                                // the indices of this thread's rows, one step ahead
+#pragma unroll
+    for (int u = 0; u < LEAF_RPT; ++u) {
+        const int64_t i = tid + (int64_t)u * LEAF_THREADS;
+        ixn[u] = (i < kb) ? __ldg(Lp + i) : 0ull;
+    }
     for (int t = 0; t < nsteps; ++t) {
         const int64_t r0 = 64 * (int64_t)t;
         const int nt = (int)min((int64_t)KS, kb - r0);
         __syncthreads();                                   // rows of this step written by the last one
         if (tid < 2 * KS) {
             const int p = tid >> 1, q = tid & 1;
-            G[p][q] = (p < nt && (q == 0 || two)) ? X[(r0 + p) * ld + q] : 0ull;
+            G[p][q] = (p < nt) ? Xs[2 * (r0 + p) + q] : 0ull;
+        }
+        uint64_t ix[LEAF_RPT];
+#pragma unroll
+        for (int u = 0; u < LEAF_RPT; ++u) {
+            ix[u] = ixn[u];
+            const int64_t i = tid + (int64_t)u * LEAF_THREADS;
+            ixn[u] = (t + 1 < nsteps && i >= r0 + 64 && i < kb) ? __ldg(Lp + (int64_t)(t + 1) * kb + i) : 0ull;
         }
         __syncthreads();
         if (tid < 128) {
@@ -196,37 +224,35 @@ trsm_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64
             }
         }
         __syncthreads();
-        const uint64_t *Lpt = Lp + (int64_t)t * kb;
-        for (int64_t i0 = r0 + tid; i0 < kb; i0 += 4 * LEAF_THREADS) {
-            uint64_t ix[4], x0[4], x1[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t i = i0 + (int64_t)u * LEAF_THREADS;
-                ix[u] = 0;
-                x0[u] = 0;
-                x1[u] = 0;
-                if (i < kb) {
-                    ix[u] = __ldg(Lpt + i);
-                    x0[u] = X[i * ld];
-                    if (two) x1[u] = X[i * ld + 1];
-                }
+        for (int u = 0; u < LEAF_RPT; ++u) {
+            const int64_t i = tid + (int64_t)u * LEAF_THREADS;
+            if (i < r0 || i >= kb) continue;
+            uint64_t x0 = Xs[2 * i], x1 = Xs[2 * i + 1];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const ulonglong2 tv =
+                    *reinterpret_cast<const ulonglong2 *>(T + (b * 256 + ((ix[u] >> (8 * b)) & 255u)) * 2);
+                x0 ^= tv.x;
+                x1 ^= tv.y;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t i = i0 + (int64_t)u * LEAF_THREADS;
-                if (i >= kb) continue;
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const ulonglong2 tv =
-                        *reinterpret_cast<const ulonglong2 *>(T + (b * 256 + ((ix[u] >> (8 * b)) & 255u)) * 2);
-                    x0[u] ^= tv.x;
-                    x1[u] ^= tv.y;
-                }
-                X[i * ld] = x0[u];
-                if (two) X[i * ld + 1] = x1[u];
-            }
+            Xs[2 * i] = x0;
+            Xs[2 * i + 1] = x1;
         }
     }
+    __syncthreads();
+    for (int u = 0; u < LEAF_RPT; ++u) {
+        const int64_t i = tid + (int64_t)u * LEAF_THREADS;
+        if (i < kb) {
+            X[i * ld] = Xs[2 * i];
+            if (two) X[i * ld + 1] = Xs[2 * i + 1];
+        }
+    }
+}
+
+cudaError_t setup_trsm_leaf_kernel()
+{
+    return cudaFuncSetAttribute(trsm_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM);
 }
 
 cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
@@ -236,8 +262,8 @@ cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t r
     cudaError_t e =
         launch_kernel(trsm_leaf_prep_kernel, dim3((int)((kb + 63) / 64)), dim3(LEAF_THREADS), 0, st, Lt, ldt, kb, Lp);
     if (e != cudaSuccess) return e;
-    return launch_kernel(trsm_leaf_kernel, dim3((int)((W - w_lo + 1) / 2)), dim3(LEAF_THREADS), 0, st, A, ld, row0,
-                         kb, (const uint64_t *)Lp, w_lo, W);
+    return launch_kernel(trsm_leaf_kernel, dim3((int)((W - w_lo + 1) / 2)), dim3(LEAF_THREADS), LEAF_SMEM, st, A, ld,
+                         row0, kb, (const uint64_t *)Lp, w_lo, W);
 }
 
 constexpr int PERM_CHUNK = 8;                          // words per CTA
