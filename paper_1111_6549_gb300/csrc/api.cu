@@ -19,7 +19,6 @@
 #include <vector>
 
 namespace gf2 {
-cudaError_t setup_trsm_leaf_kernel();   // kernels_blocked.cu: the fused leaf keeps its rows in shared memory
 thread_local bool g_pdl = false;
 }  // namespace gf2
 
@@ -67,6 +66,8 @@ struct gf2_handle {
     size_t lbuf_cap = 0;
     char *tbuf = nullptr;          // blocked PLE: indices of the fused TRSM leaf
     size_t tbuf_cap = 0;
+    char *pbuf = nullptr;          // blocked PLE: a block's composed row moves and the moved words
+    size_t pbuf_cap = 0;
     void *lt = nullptr;            // cuBLASLt state (created on first use)
     char *gbuf = nullptr;          // expanded operands and fp32 counts of the GEMM path
     size_t gbuf_cap = 0;
@@ -434,12 +435,18 @@ static int block_trailing(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, 
 {
     const int64_t W = words_for(ncols);
     {
+        const size_t pb = permute_scratch_bytes((int)s0, (int)s1, m, r0, w_lo, w_hi);
+        if (pb > 0) {
+            const int rc = grow(&h->pbuf, &h->pbuf_cap, pb, h->stream);
+            if (rc) return rc;
+        }
         Timed t(h, K_OTHER);
         CK(launch_permute_trailing(h->stream, A, ld,
                                    reinterpret_cast<StripeDesc *>(h->ws + layout_for(m, ncols).descs), (int)s0,
-                                   (int)s1, w_lo, w_hi));
+                                   (int)s1, w_lo, w_hi, m, r0, pb > 0 ? h->pbuf : nullptr, pb > 0 ? h->pbuf_cap : 0,
+                                   h->num_sms));
     }
-    h->launches += 1;
+    h->launches += permute_scratch_bytes((int)s0, (int)s1, m, r0, w_lo, w_hi) > 0 ? 4 : 1;
     const int64_t kb = r1 - r0;
     if (kb <= 0 || w_lo >= w_hi) return GF2_OK;
     // the block's L bits, rows r0 .. m, aligned
@@ -841,7 +848,7 @@ int gf2_create(gf2_handle_t *handle, int device)
         delete h;
         return GF2_ECUDA;
     }
-    if (setup_update_kernel() != cudaSuccess || setup_trsm_leaf_kernel() != cudaSuccess) {
+    if (setup_update_kernel() != cudaSuccess || setup_blocked_kernels() != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return GF2_ECUDA;
@@ -881,6 +888,7 @@ int gf2_destroy(gf2_handle_t h)
     cudaFree(h->gbuf);
     cudaFree(h->lbuf);
     cudaFree(h->tbuf);
+    cudaFree(h->pbuf);
     gemm_lt_destroy(h->lt);
     cudaFree(h->small);
     delete h;

@@ -252,8 +252,15 @@ cudaError_t launch_gather_lbits(cudaStream_t st, const uint64_t *A, int64_t ld, 
 cudaError_t launch_gather_pivbits(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int64_t row0,
                                   int64_t rows, const int64_t *Qb, int64_t kb, int64_t kw, uint64_t *out,
                                   int num_sms);
+// The row moves of the stripes [s0, s1) (their first row r0) on the words
+// [w_lo, W): composed into one permutation and applied by a gather and a
+// scatter through `scratch` when it holds permute_scratch_bytes (0: the
+// block is too wide to compose), else replayed stripe by stripe.
+size_t permute_scratch_bytes(int s0, int s1, int64_t m, int64_t r0, int64_t w_lo, int64_t W);
 cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *descs, int s0,
-                                    int s1, int64_t w_lo, int64_t W);
+                                    int s1, int64_t w_lo, int64_t W, int64_t m, int64_t r0, char *scratch,
+                                    size_t scratch_bytes, int num_sms);
+cudaError_t setup_blocked_kernels();   // shared-memory limits of the TRSM leaf and the move composition
 // fused TRSM leaf (kb <= TRSM_LEAF_ROWS): indices into Lp (kb * ceil(kb / 64)
 // words), then one launch over the words [w_lo, W)
 cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,

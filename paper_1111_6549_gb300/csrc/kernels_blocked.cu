@@ -15,6 +15,9 @@
 // (trsm_leaf_kernel).
 #include "panel_dev.cuh"
 
+#include <algorithm>
+#include <climits>
+
 namespace gf2 {
 
 // out[i][w] = bits [c0 + 64 w, c0 + 64 w + 64) of row row0 + i, masked to the
@@ -250,11 +253,6 @@ trsm_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64
     }
 }
 
-cudaError_t setup_trsm_leaf_kernel()
-{
-    return cudaFuncSetAttribute(trsm_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM);
-}
-
 cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
                              int64_t ldt, uint64_t *Lp, int64_t w_lo, int64_t W)
 {
@@ -274,10 +272,12 @@ constexpr int PERM_THREADS = 256;
 // S_src[k] (positions before that stripe's swaps) at position r + S_off[k].
 // Each CTA owns PERM_CHUNK words of every row, so CTAs never share data.
 __global__ void __launch_bounds__(PERM_THREADS)
-permute_trailing_kernel(uint64_t *A, int64_t ld, const StripeDesc *descs, int s0, int s1, int64_t w_lo, int64_t W)
+permute_trailing_kernel(uint64_t *A, int64_t ld, const StripeDesc *descs, int s0, int s1, int64_t w_lo, int64_t W,
+                        const int32_t *composed)
 {
     pdl_wait();
     pdl_trigger();
+    if (composed && *composed >= 0) return;            // the composed form did the work
     __shared__ uint64_t tmp[SMAX][PERM_CHUNK];
     const int64_t wb = w_lo + (int64_t)blockIdx.x * PERM_CHUNK;
     if (wb >= W) return;
@@ -300,13 +300,144 @@ permute_trailing_kernel(uint64_t *A, int64_t ld, const StripeDesc *descs, int s0
     }
 }
 
-cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *descs, int s0,
-                                    int s1, int64_t w_lo, int64_t W)
+// The composed form: one CTA follows every staged move of the stripes in
+// order on a map tau from positions to the rows their content comes from,
+// kept in shared memory for the positions r0 .. r0 + span - 1, then lists
+// the positions whose content changed.  A gather of the listed source rows
+// into a buffer and a scatter back apply the whole permutation to the words
+// [w_lo, W) in two passes, instead of one pass per stripe.  The window path
+// of the panel keeps every destination within 128 rows of the stripe's rank
+// (inside the span); the block-wide path may swap with a row anywhere below.
+// A destination beyond the span marks the composition failed (count -1,
+// nothing written outside the span), and the per-stripe kernel launched
+// after it then does the work instead.  A source beyond the span that was
+// never a destination still holds its own content.
+constexpr int COMPOSE_THREADS = 1024;
+constexpr size_t COMPOSE_MAX_SMEM = 200 * 1024;
+
+__global__ void __launch_bounds__(COMPOSE_THREADS)
+compose_moves_kernel(const StripeDesc *descs, int s0, int s1, int64_t r0, int span, int64_t *moves, int32_t *count)
 {
-    const int64_t blocks = (W - w_lo + PERM_CHUNK - 1) / PERM_CHUNK;
-    if (blocks <= 0 || s1 <= s0) return cudaSuccess;
-    return launch_kernel(permute_trailing_kernel, dim3((int)blocks), dim3(PERM_THREADS), 0, st, A, ld, descs, s0, s1,
-                         w_lo, W);
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ int32_t tau[];                   // tau[p]: source offset (from r0) of position r0 + p
+    __shared__ int sN, sFail;
+    const int tid = threadIdx.x;
+    for (int p = tid; p < span; p += COMPOSE_THREADS) tau[p] = p;
+    if (tid == 0) {
+        sN = 0;
+        sFail = 0;
+    }
+    // this thread's move in a stripe (staged row tid), read one stripe ahead
+    auto load = [&](int s, int64_t &dst, int64_t &src) {
+        dst = -1;
+        src = 0;
+        if (s < s1) {
+            const StripeDesc *d = descs + s;
+            const int nS = d->rbar > 0 ? d->nS : 0;
+            if (tid < nS) {
+                src = d->S_src[tid] - r0;
+                dst = d->r + d->S_off[tid] - r0;
+            }
+        }
+    };
+    int64_t dst, dn, src, sn;
+    load(s0, dst, src);
+    __syncthreads();
+    for (int s = s0; s < s1; ++s) {
+        load(s + 1, dn, sn);
+        int32_t val = 0;
+        if (dst >= 0) val = (src >= 0 && src < span) ? tau[src] : (int32_t)src;
+        __syncthreads();                               // every move of the stripe reads before any writes
+        if (dst >= 0) {
+            if (dst < span) tau[dst] = val;
+            else sFail = 1;
+        }
+        __syncthreads();
+        dst = dn;
+        src = sn;
+    }
+    if (sFail) {
+        if (tid == 0) *count = -1;
+        return;
+    }
+    for (int p = tid; p < span; p += COMPOSE_THREADS) {
+        const int32_t t = tau[p];
+        if (t != p) {
+            const int i = atomicAdd(&sN, 1);
+            moves[2 * i] = r0 + p;
+            moves[2 * i + 1] = r0 + t;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *count = sN;
+}
+
+// One warp per listed move: the source row's words [w_lo, w_lo + width)
+// into row i of buf (gather), or buf's row i to the destination (scatter).
+template <bool GATHER>
+__global__ void apply_moves_kernel(uint64_t *A, int64_t ld, const int64_t *moves, const int32_t *count, int64_t w_lo,
+                                   int64_t width, uint64_t *buf)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int K = *count;
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < K; i += (int64_t)gridDim.x * wpb) {
+        uint64_t *row = A + moves[2 * i + (GATHER ? 1 : 0)] * ld + w_lo;
+        uint64_t *b = buf + i * width;
+        for (int64_t w = lane; w < width; w += 32) {
+            if (GATHER) b[w] = row[w];
+            else row[w] = b[w];
+        }
+    }
+}
+
+cudaError_t setup_blocked_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(trsm_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(compose_moves_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)COMPOSE_MAX_SMEM);
+}
+
+size_t permute_scratch_bytes(int s0, int s1, int64_t m, int64_t r0, int64_t w_lo, int64_t W)
+{
+    const int64_t span = std::min<int64_t>(m - r0, (int64_t)KS * (s1 - s0) + SMAX);
+    if (span <= 0 || (size_t)span * sizeof(int32_t) > COMPOSE_MAX_SMEM || W <= w_lo) return 0;
+    return (size_t)span * (2 * sizeof(int64_t) + (size_t)(W - w_lo) * sizeof(uint64_t)) + 256;
+}
+
+cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, const StripeDesc *descs, int s0,
+                                    int s1, int64_t w_lo, int64_t W, int64_t m, int64_t r0, char *scratch,
+                                    size_t scratch_bytes, int num_sms)
+{
+    if (W <= w_lo || s1 <= s0) return cudaSuccess;
+    const int64_t span = std::min<int64_t>(m - r0, (int64_t)KS * (s1 - s0) + SMAX);
+    const size_t need = permute_scratch_bytes(s0, s1, m, r0, w_lo, W);
+    const int64_t pblocks = (W - w_lo + PERM_CHUNK - 1) / PERM_CHUNK;
+    if (need == 0 || scratch == nullptr || scratch_bytes < need || m - r0 > INT32_MAX) {
+        // one pass per stripe
+        return launch_kernel(permute_trailing_kernel, dim3((int)pblocks), dim3(PERM_THREADS), 0, st, A, ld, descs, s0,
+                             s1, w_lo, W, (const int32_t *)nullptr);
+    }
+    int32_t *count = reinterpret_cast<int32_t *>(scratch);
+    int64_t *moves = reinterpret_cast<int64_t *>(scratch + 256);
+    uint64_t *buf = reinterpret_cast<uint64_t *>(moves + 2 * span);
+    cudaError_t e = launch_kernel(compose_moves_kernel, dim3(1), dim3(COMPOSE_THREADS), (size_t)span * sizeof(int32_t),
+                                  st, descs, s0, s1, r0, (int)span, moves, count);
+    if (e != cudaSuccess) return e;
+    const int grid = 8 * num_sms;
+    e = launch_kernel(apply_moves_kernel<true>, dim3(grid), dim3(256), 0, st, A, ld, (const int64_t *)moves,
+                      (const int32_t *)count, w_lo, W - w_lo, buf);
+    if (e != cudaSuccess) return e;
+    e = launch_kernel(apply_moves_kernel<false>, dim3(grid), dim3(256), 0, st, A, ld, (const int64_t *)moves,
+                      (const int32_t *)count, w_lo, W - w_lo, buf);
+    if (e != cudaSuccess) return e;
+    // a composition that failed (count -1) leaves the moves to the per-stripe kernel
+    return launch_kernel(permute_trailing_kernel, dim3((int)pblocks), dim3(PERM_THREADS), 0, st, A, ld, descs, s0, s1,
+                         w_lo, W, (const int32_t *)count);
 }
 
 }  // namespace gf2
