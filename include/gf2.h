@@ -327,9 +327,10 @@ int gf2_server_destroy(gf2_server_t server);
  *                      the host then reads the rank once per block, so the
  *                      _async calls wait for each block's pivot search;
  *                      0: one table update per 64-column stripe; -1
- *                      (default): blocks of 16384 columns from 65536 pivot
+ *                      (default): blocks of 8192 columns from 65536 pivot
  *                      columns on, else 0.  The block's TRSM halves down to
- *                      1024-row leaves, each solved by one fused launch
+ *                      leaves of GF2_OPT_TRSM_LEAF rows, each solved by one
+ *                      fused launch
  *   GF2_OPT_MUL_GEMM_FORMAT  0 (default): the library's own FP4 GEMM;
  *                      4 / 8: a cuBLASLt GEMM on FP4 E2M1 (NVFP4 scales
  *                      1.0) / FP8 E4M3 operands followed by a parity pass,
@@ -367,11 +368,34 @@ int gf2_server_destroy(gf2_server_t server);
  *                      to its right sibling's columns only -- instead of
  *                      iterating over the blocks left to right, each block's
  *                      trailing update reaching the row end (default 0)
+ *   GF2_OPT_TRSM_LEAF  rows of the fused TRSM leaves of the blocked PLE
+ *                      (Algorithm 3's TRSM): 1024, 2048 (default) or 4096.
+ *                      Larger diagonal blocks are halved, the halves joined
+ *                      by the tensor-core GEMM; a leaf solves its rows in
+ *                      64-row table steps in one launch
+ *   GF2_OPT_RREF_LEAF  the RREF recovery's base blocks (GF2_OPT_RREF_BLOCK,
+ *                      automatic 8192 columns) each reduced by one fused
+ *                      back-substitution launch: the block's pivot rows
+ *                      times the inverse of their unit upper triangular bits
+ *                      on their own pivot columns, in 64-row table steps
+ *                      (default 1; 0: one table pass per stripe).  The
+ *                      plain, tcgen05 and TMA update forms keep the passes
+ *   GF2_OPT_RREF_COMPACT  the RREF recovery on the non-pivot columns only
+ *                      (default 1): the RREF is U^-1 E with U the pivot
+ *                      rows' bits on their pivot columns, the identity there,
+ *                      so E's non-pivot columns are gathered into a compact
+ *                      matrix, solved by recursive halving (fused leaves,
+ *                      products through gf2_mul) and written back beside the
+ *                      identity.  Used from 8192 pivot columns on, or with a
+ *                      positive GF2_OPT_RREF_BLOCK (then also the leaves'
+ *                      row bound, at most 8192); the host reads the rank and
+ *                      the pivot columns once, so the _async calls wait for
+ *                      the decomposition.  0: the stripe-wise recovery
  * Look-ahead is on by default; the tcgen05 and TMA forms are off (the
  * register-pipelined table update is faster on every measured shape).
  * Results are identical either way; only the speed differs.
- * GF2_EINVAL for an unknown option, a negative value, or a format other
- * than 0, 4 or 8.
+ * GF2_EINVAL for an unknown option, a negative value, a format other
+ * than 0, 4 or 8, or a leaf size other than 1024, 2048 or 4096.
  */
 #define GF2_OPT_LOOKAHEAD       1
 #define GF2_OPT_TC_MUL          2
@@ -385,6 +409,9 @@ int gf2_server_destroy(gf2_server_t server);
 #define GF2_OPT_NAIVE_UPDATE    10
 #define GF2_OPT_PDL             11
 #define GF2_OPT_PLE_RECURSIVE   12
+#define GF2_OPT_TRSM_LEAF       13
+#define GF2_OPT_RREF_LEAF       14
+#define GF2_OPT_RREF_COMPACT    15
 int gf2_set_option(gf2_handle_t handle, int option, int64_t value);
 
 /* Counters of the work enqueued since the last reset (host struct). */

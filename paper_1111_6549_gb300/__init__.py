@@ -26,7 +26,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 GF2_OK, GF2_EINVAL, GF2_ENOMEM, GF2_ECUDA, GF2_ETIMEOUT, GF2_EINTERNAL = range(6)
 (OPT_LOOKAHEAD, OPT_TC_MUL, OPT_TC_UPDATE, OPT_TMA_UPDATE, OPT_MUL_GEMM_MIN_K, OPT_PLE_BLOCK,
  OPT_MUL_GEMM_FORMAT, OPT_RREF_BLOCK, OPT_WIDE_UPDATE, OPT_NAIVE_UPDATE, OPT_PDL,
- OPT_PLE_RECURSIVE) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
+ OPT_PLE_RECURSIVE, OPT_TRSM_LEAF, OPT_RREF_LEAF, OPT_RREF_COMPACT) = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14,
+                                                                 15)
 BATCH_CLASSES, BATCH_CONFIGS = 6, 5
 SOLVE_UNIQUE, SOLVE_UNDERDETERMINED, SOLVE_INCONSISTENT = 0, 1, 2
 CARRIER_B1, CARRIER_FP4, CARRIER_FP8, CARRIER_NVF4 = 1, 4, 8, 16
@@ -340,7 +341,8 @@ class Handle:
 
     def set_option(self, option: int, value: int) -> None:
         """An OPT_* execution option (gf2_set_option): switches take 0 / 1, block widths a
-        multiple of 64 (0 off, -1 automatic), OPT_MUL_GEMM_FORMAT 4 or 8; results are identical."""
+        multiple of 64 (0 off, -1 automatic), OPT_MUL_GEMM_FORMAT 4 or 8, OPT_TRSM_LEAF 1024, 2048
+        or 4096; results are identical."""
         _check(load().gf2_set_option(self._h, option, int(value)), "gf2_set_option")
 
     # ---- statistics -----------------------------------------------------

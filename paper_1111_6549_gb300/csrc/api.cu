@@ -62,12 +62,17 @@ struct gf2_handle {
     bool pdl = true;               // launches with programmatic dependent launch (GF2_OPT_PDL)
     int64_t ple_block = -1;        // PLE column block for the blocked trailing update (0: per stripe, -1: auto)
     bool ple_recursive = false;    // blocked PLE by recursive halving (Algorithm 3) instead of iterated blocks
+    int64_t leaf_rows = 2048;      // blocked PLE: rows of the fused TRSM leaves (1024, 2048 or 4096)
+    bool rref_leaf = true;         // RREF recovery: one fused back-substitution launch per base block
     char *lbuf = nullptr;          // blocked PLE: the block's gathered L bits
     size_t lbuf_cap = 0;
     char *tbuf = nullptr;          // blocked PLE: indices of the fused TRSM leaf
     size_t tbuf_cap = 0;
     char *pbuf = nullptr;          // blocked PLE: a block's composed row moves and the moved words
     size_t pbuf_cap = 0;
+    char *cbuf = nullptr;          // compact RREF recovery: non-pivot column maps and the reduced bits
+    size_t cbuf_cap = 0;
+    bool rref_compact = true;      // RREF recovery on the non-pivot columns only (pivot columns: identity)
     void *lt = nullptr;            // cuBLASLt state (created on first use)
     char *gbuf = nullptr;          // expanded operands and fp32 counts of the GEMM path
     size_t gbuf_cap = 0;
@@ -409,12 +414,12 @@ int run_ple_range(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
 static int trsm_lower(gf2_handle *h, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
                       int64_t ldt, int64_t w_lo, int64_t W, int64_t ncols)
 {
-    if (kb > TRSM_LEAF_ROWS) {
+    if (kb > h->leaf_rows) {
         const int64_t hh = ((kb / 2) + 63) & ~int64_t(63);
         int rc = trsm_lower(h, A, ld, row0, hh, Lt, ldt, w_lo, W, ncols);
         if (rc) return rc;
         // the product always through the tensor-core GEMM: even at the
-        // smallest split (k = TRSM_LEAF_ROWS) it beats 64-row table passes
+        // smallest split (k = 1024) it beats 64-row table passes
         rc = mul_own(h, A + (row0 + hh) * ld + w_lo, ld, Lt + hh * ldt, ldt, A + row0 * ld + w_lo, ld, kb - hh, hh,
                      ncols - 64 * w_lo);
         if (rc) return rc;
@@ -498,11 +503,12 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
             int64_t *Q)
 {
     const int64_t W = words_for(ncols), ns = words_for(npiv);
-    // stripes per block; automatic: blocks of 16384 columns from 65536 pivot
+    // stripes per block; automatic: blocks of 8192 columns from 65536 pivot
     // columns on (measured on GB300 with the own GEMM and the fused TRSM
-    // leaves: 65536^2 PLE 75.1 ms against 83.6 ms with two blocks and 97 ms
-    // per stripe; at 32768^2 blocking does not pay)
-    const int64_t bs = h->ple_block >= 0 ? h->ple_block / 64 : (npiv >= 65536 ? 256 : 0);
+    // leaves: 65536^2 PLE 62.3 ms against 63.6 ms with 16384-column blocks,
+    // 62.6 ms with 12288 and 97 ms per stripe; at 32768^2 blocking does not
+    // pay)
+    const int64_t bs = h->ple_block >= 0 ? h->ple_block / 64 : (npiv >= 65536 ? 128 : 0);
     if (bs <= 0 || ns <= bs) return run_ple_range(h, A, m, ncols, ld, npiv, P, Q, 0, ns, W, true);
     if (h->ple_recursive) {
         // rec(a, b, w_hi): the stripes [a, b), whose updates reach the word
@@ -539,6 +545,112 @@ int run_ple(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, in
     return GF2_OK;
 }
 
+// The compact RREF recovery (Section 5's RREF from the PLE decomposition):
+// with E the decomposed matrix's first r rows (L bits cleared) and
+// U = E[:, Q] their unit upper triangular bits on the pivot columns, the RREF
+// is U^-1 E.  On the pivot columns that is the identity, so only the
+// non-pivot columns are computed: C = E[:, NP] is gathered into a compact
+// matrix, C <- U^-1 C by recursive halving of the rows (the lower half
+// reduced first, the upper rows then cleared on its pivot columns by one
+// product C1 ^= X C2 through gf2_mul, X their bits on those columns),
+// with fused back-substitution leaves of at most `leaf` rows, and the rows
+// are written back as the identity on Q plus C on NP.  The host reads the
+// rank and the pivot columns once.
+static int rref_compact(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, const int64_t *Qs,
+                        int64_t leaf)
+{
+    const int64_t W = words_for(ncols);
+    int64_t r = 0;
+    CK(cudaMemcpyAsync(&r, r_dev(h), sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (r <= 0) return GF2_OK;                           // every row cleared already
+    std::vector<int64_t> q((size_t)r);
+    CK(cudaMemcpyAsync(q.data(), Qs, (size_t)r * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // the non-pivot columns, and per word their mask and first compact position
+    std::vector<int64_t> np;
+    np.reserve((size_t)(ncols - r));
+    std::vector<uint64_t> npmask((size_t)W, 0ull);
+    std::vector<int64_t> npstart((size_t)W, 0);
+    {
+        size_t j = 0;
+        for (int64_t c = 0; c < ncols; ++c) {
+            if (j < q.size() && q[j] == c) { ++j; continue; }
+            if (npmask[(size_t)(c >> 6)] == 0) npstart[(size_t)(c >> 6)] = (int64_t)np.size();
+            npmask[(size_t)(c >> 6)] |= 1ull << (c & 63);
+            np.push_back(c);
+        }
+    }
+    const int64_t nnp = (int64_t)np.size();
+    const int64_t kwn = std::max<int64_t>(words_for(nnp), 1);
+    const size_t off_mask = align256(std::max<size_t>(np.size(), 1) * 8);
+    const size_t off_start = off_mask + align256((size_t)W * 8);
+    const size_t off_c = off_start + align256((size_t)W * 8);
+    int rc = grow(&h->cbuf, &h->cbuf_cap, off_c + (size_t)r * kwn * 8, h->stream);
+    if (rc) return rc;
+    int64_t *d_np = reinterpret_cast<int64_t *>(h->cbuf);
+    uint64_t *d_mask = reinterpret_cast<uint64_t *>(h->cbuf + off_mask);
+    int64_t *d_start = reinterpret_cast<int64_t *>(h->cbuf + off_start);
+    uint64_t *C = reinterpret_cast<uint64_t *>(h->cbuf + off_c);
+    if (nnp > 0) CK(cudaMemcpyAsync(d_np, np.data(), (size_t)nnp * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d_mask, npmask.data(), (size_t)W * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d_start, npstart.data(), (size_t)W * 8, cudaMemcpyHostToDevice, h->stream));
+    if (nnp > 0) {
+        {
+            Timed t(h, K_OTHER);
+            CK(launch_gather_pivbits(h->stream, A, ld, W, 0, r, d_np, nnp, kwn, C, h->num_sms));
+        }
+        h->launches += 1;
+        std::function<int(int64_t, int64_t)> solve = [&](int64_t ra, int64_t rb) -> int {
+            const int64_t kb = rb - ra;
+            if (kb <= 0) return GF2_OK;
+            if (kb <= leaf) {
+                const int64_t kw = words_for(kb);
+                int rc2 = grow(&h->lbuf, &h->lbuf_cap, (size_t)kb * kw * 8, h->stream);
+                if (rc2) return rc2;
+                rc2 = grow(&h->tbuf, &h->tbuf_cap, (size_t)kb * kw * 8, h->stream);
+                if (rc2) return rc2;
+                uint64_t *Xb = reinterpret_cast<uint64_t *>(h->lbuf);
+                {
+                    Timed t(h, K_OTHER);
+                    CK(launch_gather_pivbits(h->stream, A, ld, W, ra, kb, Qs + ra, kb, kw, Xb, h->num_sms));
+                }
+                {
+                    Timed t(h, K_RPASS);
+                    CK(launch_rref_leaf(h->stream, C, kwn, ra, kb, Xb, kw, nullptr,
+                                        reinterpret_cast<uint64_t *>(h->tbuf), 0, kwn, true));
+                }
+                h->launches += 3;
+                h->rpass_launches += 1;
+                if (h->profiling) h->rpass_timed += 1;
+                return GF2_OK;
+            }
+            const int64_t mid = ra + (((kb / 2) + 63) & ~int64_t(63));
+            int rc2 = solve(mid, rb);
+            if (rc2) return rc2;
+            const int64_t rows = mid - ra, kx = rb - mid, kwx = words_for(kx);
+            rc2 = grow(&h->lbuf, &h->lbuf_cap, (size_t)rows * kwx * 8, h->stream);
+            if (rc2) return rc2;
+            uint64_t *X = reinterpret_cast<uint64_t *>(h->lbuf);
+            {
+                Timed t(h, K_OTHER);
+                CK(launch_gather_pivbits(h->stream, A, ld, W, ra, rows, Qs + mid, kx, kwx, X, h->num_sms));
+            }
+            h->launches += 1;
+            rc2 = gf2_mul(h, C + ra * kwn, kwn, X, kwx, C + mid * kwn, kwn, rows, kx, nnp, 1);
+            if (rc2) return rc2;
+            return solve(ra, mid);
+        };
+        if ((rc = solve(0, r))) return rc;
+    }
+    {
+        Timed t(h, K_OTHER);
+        CK(launch_rref_scatter(h->stream, A, ld, W, r, Qs, C, kwn, d_mask, d_start, h->num_sms));
+    }
+    h->launches += 1;
+    return GF2_OK;
+}
+
 // Enqueue the RREF recovery of a matrix that run_ple just decomposed.
 int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t ld, int64_t npiv, const int64_t *Qs)
 {
@@ -552,6 +664,12 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         CK(launch_rref_lclear(h->stream, A, m, W, ld, r_dev(h), h->num_sms));
     }
     h->launches += 1;
+    // the compact form (default from 8192 pivot columns on, or with an
+    // explicit base block width, which then bounds its leaves)
+    const bool leaf_ok = h->rref_leaf && !h->naive_update && !h->tc_update && !h->tma;
+    if (h->rref_compact && leaf_ok && (h->rref_block > 0 || (h->rref_block < 0 && npiv >= 8192)))
+        return rref_compact(h, A, m, ncols, ld, Qs,
+                            std::min<int64_t>(h->rref_block > 0 ? h->rref_block : 2048, RREF_LEAF_MAX));
     // one stripe's back-substitution: rows [row_lo, r_s) over the words
     // [c_s, W) except [skip_lo, skip_hi), where those rows and the stripe's
     // pivot rows are known to be zero
@@ -672,6 +790,39 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
     // through gf2_mul -- and recurses into the left half.  Table passes and
     // products skip the words from stripe b's first column up to the first
     // column at or after it that is no pivot: zero in every row involved.
+    // A base block's own back-substitution is one fused leaf launch
+    // (rref_leaf_kernel) where the options allow it: its rows (at most 64 per
+    // stripe) are reduced over the block's words and, past the skipped words,
+    // over [sk, W); otherwise one table pass per stripe.
+    auto leaf_block = [&](int64_t a, int64_t b, int64_t ra, int64_t rb, int64_t sk) -> int {
+        const int64_t kb = rb - ra, kw = words_for(kb);
+        int rc = grow(&h->lbuf, &h->lbuf_cap, (size_t)kb * kw * 8, h->stream);
+        if (rc) return rc;
+        rc = grow(&h->tbuf, &h->tbuf_cap, (size_t)kb * kw * 8, h->stream);
+        if (rc) return rc;
+        uint64_t *Xb = reinterpret_cast<uint64_t *>(h->lbuf);
+        uint64_t *Lp = reinterpret_cast<uint64_t *>(h->tbuf);
+        {
+            Timed t(h, K_OTHER);
+            CK(launch_gather_pivbits(h->stream, A, ld, W, ra, kb, Qs + ra, kb, kw, Xb, h->num_sms));
+        }
+        const int64_t w_end = b < ns ? b : W;
+        {
+            Timed t(h, K_RPASS);
+            CK(launch_rref_leaf(h->stream, A, ld, ra, kb, Xb, kw, Qs + ra, Lp, a, w_end, true));
+        }
+        h->launches += 3;
+        h->rpass_launches += 1;
+        if (h->profiling) h->rpass_timed += 1;
+        if (w_end < W && sk < W) {
+            Timed t(h, K_RPASS);
+            CK(launch_rref_leaf(h->stream, A, ld, ra, kb, Xb, kw, Qs + ra, Lp, sk, W, false));
+            h->launches += 1;
+            h->rpass_launches += 1;
+            if (h->profiling) h->rpass_timed += 1;
+        }
+        return GF2_OK;
+    };
     // automatic: base blocks of 8192 columns from 32768 pivot columns on
     // (measured on GB300: 65536^2 RREF step 105.7 ms against 108.1 ms with
     // 16384-column blocks; 32768^2 faster than the flat recovery)
@@ -702,7 +853,10 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
             const int64_t ra = rs[(size_t)a], rb = rs[(size_t)b];
             if (rb == ra) return GF2_OK;                     // no pivot rows: nothing to reduce
             const int64_t sk = skip_end(b);
-            if (b - a <= base) return passes(a, b, ra, b < ns ? b : W, sk);
+            if (b - a <= base) {
+                if (leaf_ok && rb - ra <= RREF_LEAF_MAX) return leaf_block(a, b, ra, rb, sk);
+                return passes(a, b, ra, b < ns ? b : W, sk);
+            }
             const int64_t mid = (a + b + 1) / 2;
             int rc = rec(mid, b);
             if (rc) return rc;
@@ -893,6 +1047,7 @@ int gf2_destroy(gf2_handle_t h)
     cudaFree(h->bws);
     cudaFree(h->gbuf);
     cudaFree(h->lbuf);
+    cudaFree(h->cbuf);
     cudaFree(h->tbuf);
     cudaFree(h->pbuf);
     gemm_lt_destroy(h->lt);
@@ -1681,6 +1836,12 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
     case GF2_OPT_NAIVE_UPDATE: h->naive_update = value != 0; return GF2_OK;
     case GF2_OPT_PDL: h->pdl = value != 0; return GF2_OK;
     case GF2_OPT_PLE_RECURSIVE: h->ple_recursive = value != 0; return GF2_OK;
+    case GF2_OPT_RREF_LEAF: h->rref_leaf = value != 0; return GF2_OK;
+    case GF2_OPT_RREF_COMPACT: h->rref_compact = value != 0; return GF2_OK;
+    case GF2_OPT_TRSM_LEAF:
+        if (value != 1024 && value != 2048 && value != 4096) return GF2_EINVAL;
+        h->leaf_rows = value;
+        return GF2_OK;
     case GF2_OPT_MUL_GEMM_FORMAT:
         if (value != 8 && value != 4 && value != 0) return GF2_EINVAL;
         if (value != 0 && !kLibraryGemm) return GF2_EINVAL;   // library GEMM not built in

@@ -208,6 +208,11 @@ cudaError_t launch_tc_mul(cudaStream_t st, uint64_t *C, int64_t ldc, const uint6
                           int64_t ldb, int64_t m, int64_t k, int64_t n, int32_t *err, int num_sms);
 cudaError_t setup_update_tma_kernel();
 cudaError_t launch_update_tma(cudaStream_t st, const UpdArgs &a, int grid);   // a.tmap must be set
+// compact RREF recovery: rows i < r rewritten as the identity on their pivot
+// columns Q and the reduced non-pivot bits C (kwn words per row) elsewhere
+cudaError_t launch_rref_scatter(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int64_t r, const int64_t *Q,
+                                const uint64_t *C, int64_t kwn, const uint64_t *npmask, const int64_t *npstart,
+                                int num_sms);
 cudaError_t launch_rref_lclear(cudaStream_t st, uint64_t *A, int64_t m, int64_t W, int64_t ld,
                                const int64_t *r_dev, int num_sms);
 cudaError_t launch_rref_prep(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int s,
@@ -261,11 +266,19 @@ cudaError_t launch_permute_trailing(cudaStream_t st, uint64_t *A, int64_t ld, co
                                     int s1, int64_t w_lo, int64_t W, int64_t m, int64_t r0, char *scratch,
                                     size_t scratch_bytes, int num_sms);
 cudaError_t setup_blocked_kernels();   // shared-memory limits of the TRSM leaf and the move composition
-// fused TRSM leaf (kb <= TRSM_LEAF_ROWS): indices into Lp (kb * ceil(kb / 64)
+// fused TRSM leaf (kb <= TRSM_LEAF_MAX): indices into Lp (kb * ceil(kb / 64)
 // words), then one launch over the words [w_lo, W)
 cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
                              int64_t ldt, uint64_t *Lp, int64_t w_lo, int64_t W);
-constexpr int64_t TRSM_LEAF_ROWS = 1024;
+constexpr int64_t TRSM_LEAF_MAX = 4096;        // rows of the largest fused leaf
+// fused RREF leaf: the back-substitution of the kb <= RREF_LEAF_MAX pivot
+// rows A[row0 .. row0 + kb) (pivot columns Qb, their bits on those columns
+// gathered in Xb, kw words per row) over the words [w_lo, w_hi); prep = false
+// reuses the indices Lp (kb * ceil(kb / 64) words) of an earlier call on the
+// same rows
+constexpr int64_t RREF_LEAF_MAX = 8192;
+cudaError_t launch_rref_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Xb,
+                             int64_t kw, const int64_t *Qb, uint64_t *Lp, int64_t w_lo, int64_t w_hi, bool prep);
 cudaError_t launch_wait_selftest(cudaStream_t st, int32_t *err, unsigned long long limit_ns);
 cudaError_t launch_m4ri_prep(cudaStream_t st, const uint64_t *A, int64_t ld, int64_t W, int s,
                              const StripeDesc *descs, const int32_t *map, uint64_t *S, int64_t ldS, uint64_t *G,

@@ -99,7 +99,7 @@ cudaError_t launch_gather_pivbits(cudaStream_t st, const uint64_t *A, int64_t ld
 }
 
 // ---------------------------------------------------------------------------
-// Fused TRSM leaf: X <- L^-1 X for the kb <= TRSM_LEAF_ROWS rows X = A[row0 ..
+// Fused TRSM leaf: X <- L^-1 X for the kb <= TRSM_LEAF_MAX rows X = A[row0 ..
 // row0 + kb) over the words [w_lo, W), L unit lower triangular with its
 // strictly lower bits gathered in Lt (kb x ldt words).  Forward substitution
 // in steps of 64 rows: step t replaces rows 64 t .. 64 t + 63 by their
@@ -156,99 +156,122 @@ trsm_leaf_prep_kernel(const uint64_t *__restrict__ Lt, int64_t ldt, int64_t kb, 
 }
 
 // One CTA per pair of words; see the comment above.  The CTA's two words of
-// the leaf's rows (at most TRSM_LEAF_ROWS x 16 bytes) stay in shared memory
+// the leaf's rows (at most TRSM_LEAF_MAX x 16 bytes) stay in shared memory
 // for all steps: loaded once, updated in place, stored once.  Thread t owns
 // the rows t, t + 256, ... in every step, so it loads the next step's
 // indices of its rows while the current step runs.
-constexpr int LEAF_RPT = (int)(TRSM_LEAF_ROWS / LEAF_THREADS);
-constexpr size_t LEAF_SMEM = (size_t)TRSM_LEAF_ROWS * 2 * sizeof(uint64_t);
+//
+// Shared-memory banks.  A 16-byte access of a warp is served in four phases
+// of eight lanes; a phase costs one wavefront when its eight lanes fall into
+// eight different groups of four banks.  The tables are laid out entry-major,
+// T[8 e + t] for entry e of table t, so the slot of table t is always in bank
+// group t.  A row's eight lookups are taken in an order rotated by its lane
+// (round k reads table (k + lane) mod 8), so the eight lanes of a phase read
+// eight different tables whatever their indices are.  The build keeps the
+// same property: lane l writes table l mod 8, entries 32 w + 4 g + l / 8 of
+// warp w in Gray-code order g, from the step's rows kept at slot 9 t + b for
+// row 8 t + b (bank group t + b, distinct across the eight tables of a
+// phase).
+constexpr int LEAF_RPT_MAX = (int)(TRSM_LEAF_MAX / LEAF_THREADS);
+static_assert(LEAF_THREADS == 256, "the table build gives each of eight warps 32 entries of every table");
 
+__device__ __forceinline__ uint64_t rotr64(uint64_t x, int s)
+{
+    return s == 0 ? x : (x >> s) | (x << (64 - s));
+}
+
+template <int RPT>
 __global__ void __launch_bounds__(LEAF_THREADS)
 trsm_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *__restrict__ Lp, int64_t w_lo,
                  int64_t W)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ __align__(16) uint64_t T[8 * 256 * 2];      // eight 8-bit tables of 16-byte entries
-    __shared__ uint64_t G[KS][2];
-    extern __shared__ __align__(16) uint64_t Xs[];       // [row][2]: the CTA's two words of the leaf's rows
-    const int tid = threadIdx.x;
+    __shared__ __align__(16) ulonglong2 T[256 * 8];         // eight 8-bit tables, entry-major
+    __shared__ __align__(16) ulonglong2 Gp[72];             // the step's rows: row 8 t + b at slot 9 t + b
+    extern __shared__ __align__(16) ulonglong2 Xs[];        // [row]: the CTA's two words of the leaf's rows
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t w0 = w_lo + 2 * (int64_t)blockIdx.x;
     if (w0 >= W) return;
     const bool two = w0 + 1 < W;
     uint64_t *X = A + row0 * ld + w0;
-    for (int u = 0; u < LEAF_RPT; ++u) {
+    for (int u = 0; u < RPT; ++u) {
         const int64_t i = tid + (int64_t)u * LEAF_THREADS;
-        if (i < kb) {
-            Xs[2 * i] = X[i * ld];
-            Xs[2 * i + 1] = two ? X[i * ld + 1] : 0ull;
-        }
+        if (i < kb) Xs[i] = make_ulonglong2(X[i * ld], two ? X[i * ld + 1] : 0ull);
     }
     const int nsteps = (int)((kb + 63) / 64);
-    uint64_t ixn[LEAF_RPT];                                // the indices of this thread's rows, one step ahead
+    const int rot = 8 * (lane & 7);
+    uint64_t ixn[RPT];                                      // the indices of this thread's rows, one step ahead
 #pragma unroll
-    for (int u = 0; u < LEAF_RPT; ++u) {
+    for (int u = 0; u < RPT; ++u) {
         const int64_t i = tid + (int64_t)u * LEAF_THREADS;
         ixn[u] = (i < kb) ? __ldg(Lp + i) : 0ull;
     }
     for (int t = 0; t < nsteps; ++t) {
         const int64_t r0 = 64 * (int64_t)t;
         const int nt = (int)min((int64_t)KS, kb - r0);
-        __syncthreads();                                   // rows of this step written by the last one
-        if (tid < 2 * KS) {
-            const int p = tid >> 1, q = tid & 1;
-            G[p][q] = (p < nt) ? Xs[2 * (r0 + p) + q] : 0ull;
+        __syncthreads();                                    // rows of this step written by the last one
+        if (tid < KS) {
+            const ulonglong2 z = make_ulonglong2(0ull, 0ull);
+            Gp[9 * (tid >> 3) + (tid & 7)] = tid < nt ? Xs[r0 + tid] : z;
         }
-        uint64_t ix[LEAF_RPT];
+        uint64_t ix[RPT];
 #pragma unroll
-        for (int u = 0; u < LEAF_RPT; ++u) {
+        for (int u = 0; u < RPT; ++u) {
             ix[u] = ixn[u];
             const int64_t i = tid + (int64_t)u * LEAF_THREADS;
             ixn[u] = (t + 1 < nsteps && i >= r0 + 64 && i < kb) ? __ldg(Lp + (int64_t)(t + 1) * kb + i) : 0ull;
         }
         __syncthreads();
-        if (tid < 128) {
-            // table tau (rows 8 tau .. 8 tau + 7), 32-entry segment sg, word q:
-            // Gray-code walk from the segment's base entry
-            const int q = tid & 1, sg = (tid >> 1) & 7, tau = tid >> 4;
-            uint64_t g[8];
+        {
+            const int tt = lane & 7, sub = lane >> 3;
+            const ulonglong2 *g = Gp + 9 * tt;
+            uint64_t v0 = 0, v1 = 0;
+            auto add = [&](int c) {
+                const ulonglong2 x = g[c];
+                v0 ^= x.x;
+                v1 ^= x.y;
+            };
+            if (sub & 1) add(0);
+            if (sub & 2) add(1);
+            if (warp & 1) add(5);
+            if (warp & 2) add(6);
+            if (warp & 4) add(7);
+            int e = 32 * warp + sub;
+            T[8 * e + tt] = make_ulonglong2(v0, v1);
 #pragma unroll
-            for (int b = 0; b < 8; ++b) g[b] = G[8 * tau + b][q];
-            uint64_t val = ((sg & 1) ? g[5] : 0ull) ^ ((sg & 2) ? g[6] : 0ull) ^ ((sg & 4) ? g[7] : 0ull);
-            uint64_t *Tt = T + (tau * 256 + 32 * sg) * 2 + q;
-            int x = 0;
-            Tt[0] = val;
-#pragma unroll
-            for (int i = 1; i < 32; ++i) {
-                const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4;
-                x ^= 1 << b;
-                val ^= g[b];
-                Tt[x * 2] = val;
+            for (int j = 1; j < 8; ++j) {
+                // Gray code: step j flips bit b = number of trailing zeros of j (entry bit 2 + b)
+                const int b = (j & 1) ? 0 : (j & 2) ? 1 : 2;
+                add(2 + b);
+                e ^= 4 << b;
+                T[8 * e + tt] = make_ulonglong2(v0, v1);
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < LEAF_RPT; ++u) {
+        for (int u = 0; u < RPT; ++u) {
             const int64_t i = tid + (int64_t)u * LEAF_THREADS;
             if (i < r0 || i >= kb) continue;
-            uint64_t x0 = Xs[2 * i], x1 = Xs[2 * i + 1];
+            ulonglong2 x = Xs[i];
+            const uint64_t ir = rotr64(ix[u], rot);         // byte k: the index byte of table (k + lane) mod 8
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const ulonglong2 tv =
-                    *reinterpret_cast<const ulonglong2 *>(T + (b * 256 + ((ix[u] >> (8 * b)) & 255u)) * 2);
-                x0 ^= tv.x;
-                x1 ^= tv.y;
+            for (int k = 0; k < 8; ++k) {
+                const int e = (int)((ir >> (8 * k)) & 255u);
+                const ulonglong2 tv = T[8 * e + ((k + lane) & 7)];
+                x.x ^= tv.x;
+                x.y ^= tv.y;
             }
-            Xs[2 * i] = x0;
-            Xs[2 * i + 1] = x1;
+            Xs[i] = x;
         }
     }
     __syncthreads();
-    for (int u = 0; u < LEAF_RPT; ++u) {
+    for (int u = 0; u < RPT; ++u) {
         const int64_t i = tid + (int64_t)u * LEAF_THREADS;
         if (i < kb) {
-            X[i * ld] = Xs[2 * i];
-            if (two) X[i * ld + 1] = Xs[2 * i + 1];
+            const ulonglong2 x = Xs[i];
+            X[i * ld] = x.x;
+            if (two) X[i * ld + 1] = x.y;
         }
     }
 }
@@ -256,12 +279,220 @@ trsm_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64
 cudaError_t launch_trsm_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Lt,
                              int64_t ldt, uint64_t *Lp, int64_t w_lo, int64_t W)
 {
-    if (kb <= 0 || kb > TRSM_LEAF_ROWS || w_lo >= W) return cudaSuccess;
+    if (kb <= 0 || kb > TRSM_LEAF_MAX || w_lo >= W) return cudaSuccess;
     cudaError_t e =
         launch_kernel(trsm_leaf_prep_kernel, dim3((int)((kb + 63) / 64)), dim3(LEAF_THREADS), 0, st, Lt, ldt, kb, Lp);
     if (e != cudaSuccess) return e;
-    return launch_kernel(trsm_leaf_kernel, dim3((int)((W - w_lo + 1) / 2)), dim3(LEAF_THREADS), LEAF_SMEM, st, A, ld,
-                         row0, kb, (const uint64_t *)Lp, w_lo, W);
+    const dim3 grid((unsigned)((W - w_lo + 1) / 2));
+    const size_t smem = (size_t)kb * sizeof(ulonglong2);
+    const uint64_t *Lpc = Lp;
+    if (kb <= 4 * LEAF_THREADS)
+        return launch_kernel(trsm_leaf_kernel<4>, grid, dim3(LEAF_THREADS), smem, st, A, ld, row0, kb, Lpc, w_lo, W);
+    if (kb <= 8 * LEAF_THREADS)
+        return launch_kernel(trsm_leaf_kernel<8>, grid, dim3(LEAF_THREADS), smem, st, A, ld, row0, kb, Lpc, w_lo, W);
+    return launch_kernel(trsm_leaf_kernel<LEAF_RPT_MAX>, grid, dim3(LEAF_THREADS), smem, st, A, ld, row0, kb, Lpc,
+                         w_lo, W);
+}
+
+// ---------------------------------------------------------------------------
+// Fused RREF leaf: the back-substitution of one base block of the RREF
+// recovery in one launch.  The block's pivot rows X = A[row0 .. row0 + kb)
+// are in echelon form; T, their bits on their own pivot columns, is unit
+// upper triangular, and the reduced rows are T^-1 X (they then hold the
+// identity on those columns and span the same rows).  Backward substitution
+// in steps of 64 rows from the last: step j replaces rows 64 j .. 64 j + 63
+// by their product with the inverse of T's diagonal block j and adds to every
+// row above its bits on that block's pivot columns times those new rows.  A
+// row's bits on the pivot columns of a later step are never changed by the
+// steps after it (the rows added are zero left of their own pivots), so
+// every step's table index is known from the unreduced block:
+// rref_leaf_prep_kernel forms them all from the gathered bits (one CTA per
+// step), and rref_leaf_kernel walks the steps with each CTA owning two words
+// of every row, as the TRSM leaf does.  A step whose first pivot column lies
+// right of a CTA's words changes nothing there, so a CTA starts at the last
+// step that reaches its words.
+
+// Lp[j * kb + i] for the rows i < 64 j + 64 of the block: the index of row i
+// in step j.  Xb holds the gathered bits (row i, bit q of word w: row i's bit
+// on pivot column 64 w + q of the block), kw words per row.
+__global__ void __launch_bounds__(LEAF_THREADS)
+rref_leaf_prep_kernel(const uint64_t *__restrict__ Xb, int64_t kw, int64_t kb, uint64_t *__restrict__ Lp)
+{
+    pdl_wait();
+    pdl_trigger();
+    __shared__ uint64_t sR[KS], sM[KS], sUi[KS];
+    __shared__ uint64_t tab[8][256];
+    const int j = blockIdx.x, tid = threadIdx.x;
+    const int64_t r0 = 64 * (int64_t)j;
+    const int nt = (int)min((int64_t)KS, kb - r0);
+    // the diagonal block reversed (row and column order), a unit lower
+    // triangular matrix R with R^-1 the reversal of the block's inverse;
+    // rows past the block's end are identity rows
+    if (tid < KS) {
+        const int p = KS - 1 - tid;
+        const uint64_t u = p < nt ? Xb[(r0 + p) * kw + j] : (1ull << p);
+        sR[tid] = __brevll(u);
+    }
+    __syncthreads();
+    if (tid < 32) warp_lower_inverse_blocked(sR, KS, sM);
+    __syncthreads();
+    if (tid < KS) sUi[tid] = __brevll(sM[KS - 1 - tid]);
+    __syncthreads();
+    for (int e2 = tid; e2 < 8 * 256; e2 += blockDim.x) {
+        const int b = e2 >> 8, e = e2 & 255;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (((e >> q) & 1) && 8 * b + q < nt) acc ^= sUi[8 * b + q];
+        tab[b][e] = acc;
+    }
+    __syncthreads();
+    const uint64_t vmask = nt == 64 ? ~0ull : ((1ull << nt) - 1ull);
+    for (int64_t i = tid; i < r0 + nt; i += blockDim.x) {
+        uint64_t v;
+        if (i >= r0) {
+            const int off = (int)(i - r0);
+            v = sUi[off] ^ (1ull << off);
+        } else {
+            const uint64_t x = Xb[i * kw + j] & vmask;
+            v = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) v ^= tab[b][(x >> (8 * b)) & 255u];
+        }
+        Lp[(int64_t)j * kb + i] = v;
+    }
+}
+
+constexpr int RLEAF_THREADS = 512;
+constexpr int RLEAF_RPT = (int)(RREF_LEAF_MAX / RLEAF_THREADS);
+
+// One CTA per pair of words [w0, w0 + 2) of [w_lo, w_hi); Qb: the block's
+// pivot columns (increasing), or null when the words are not the matrix's
+// own (a compacted column set: every step reaches every word).  Layout of the
+// tables and of the step's rows as in trsm_leaf_kernel (conflict-free lookups
+// and build).
+__global__ void __launch_bounds__(RLEAF_THREADS, 1)
+rref_leaf_kernel(uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *__restrict__ Lp,
+                 const int64_t *__restrict__ Qb, int64_t w_lo, int64_t w_hi)
+{
+    pdl_wait();
+    pdl_trigger();
+    __shared__ __align__(16) ulonglong2 T[256 * 8];
+    __shared__ __align__(16) ulonglong2 Gp[72];
+    extern __shared__ __align__(16) ulonglong2 Xs[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t w0 = w_lo + 2 * (int64_t)blockIdx.x;
+    if (w0 >= w_hi) return;
+    const bool two = w0 + 1 < w_hi;
+    const int64_t wlast = two ? w0 + 1 : w0;
+    // the last step whose rows reach these words (their first pivot column
+    // at or before the last word)
+    const int nsteps = (int)((kb + 63) / 64);
+    int jmax = Qb ? -1 : nsteps - 1;
+    if (Qb) {
+        int lo = 0, hi = nsteps - 1;                     // largest j with Qb[64 j] / 64 <= wlast
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((__ldg(Qb + 64 * (int64_t)mid) >> 6) <= wlast) { jmax = mid; lo = mid + 1; }
+            else hi = mid - 1;
+        }
+    }
+    if (jmax < 0) return;
+    const int64_t nrow = min(kb, 64 * (int64_t)jmax + 64);   // rows that steps 0 .. jmax touch
+    uint64_t *X = A + row0 * ld + w0;
+#pragma unroll
+    for (int u = 0; u < RLEAF_RPT; ++u) {
+        const int64_t i = tid + (int64_t)u * RLEAF_THREADS;
+        if (i < nrow) Xs[i] = make_ulonglong2(X[i * ld], two ? X[i * ld + 1] : 0ull);
+    }
+    const int rot = 8 * (lane & 7);
+    uint64_t ixn[RLEAF_RPT];
+#pragma unroll
+    for (int u = 0; u < RLEAF_RPT; ++u) {
+        const int64_t i = tid + (int64_t)u * RLEAF_THREADS;
+        ixn[u] = (i < nrow) ? __ldg(Lp + (int64_t)jmax * kb + i) : 0ull;
+    }
+    for (int j = jmax; j >= 0; --j) {
+        const int64_t r0 = 64 * (int64_t)j;
+        const int nt = (int)min((int64_t)KS, kb - r0);
+        __syncthreads();                                 // rows of this step written by the last one
+        if (tid < KS) {
+            const ulonglong2 z = make_ulonglong2(0ull, 0ull);
+            Gp[9 * (tid >> 3) + (tid & 7)] = tid < nt ? Xs[r0 + tid] : z;
+        }
+        uint64_t ix[RLEAF_RPT];
+#pragma unroll
+        for (int u = 0; u < RLEAF_RPT; ++u) {
+            ix[u] = ixn[u];
+            const int64_t i = tid + (int64_t)u * RLEAF_THREADS;
+            ixn[u] = (j > 0 && i < r0) ? __ldg(Lp + (int64_t)(j - 1) * kb + i) : 0ull;
+        }
+        __syncthreads();
+        if (warp < 8) {
+            const int tt = lane & 7, sub = lane >> 3;
+            const ulonglong2 *g = Gp + 9 * tt;
+            uint64_t v0 = 0, v1 = 0;
+            auto add = [&](int c) {
+                const ulonglong2 x = g[c];
+                v0 ^= x.x;
+                v1 ^= x.y;
+            };
+            if (sub & 1) add(0);
+            if (sub & 2) add(1);
+            if (warp & 1) add(5);
+            if (warp & 2) add(6);
+            if (warp & 4) add(7);
+            int e = 32 * warp + sub;
+            T[8 * e + tt] = make_ulonglong2(v0, v1);
+#pragma unroll
+            for (int s = 1; s < 8; ++s) {
+                const int b = (s & 1) ? 0 : (s & 2) ? 1 : 2;
+                add(2 + b);
+                e ^= 4 << b;
+                T[8 * e + tt] = make_ulonglong2(v0, v1);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < RLEAF_RPT; ++u) {
+            const int64_t i = tid + (int64_t)u * RLEAF_THREADS;
+            if (i >= r0 + nt) continue;
+            ulonglong2 x = Xs[i];
+            const uint64_t ir = rotr64(ix[u], rot);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = (int)((ir >> (8 * k)) & 255u);
+                const ulonglong2 tv = T[8 * e + ((k + lane) & 7)];
+                x.x ^= tv.x;
+                x.y ^= tv.y;
+            }
+            Xs[i] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < RLEAF_RPT; ++u) {
+        const int64_t i = tid + (int64_t)u * RLEAF_THREADS;
+        if (i < nrow) {
+            const ulonglong2 x = Xs[i];
+            X[i * ld] = x.x;
+            if (two) X[i * ld + 1] = x.y;
+        }
+    }
+}
+
+cudaError_t launch_rref_leaf(cudaStream_t st, uint64_t *A, int64_t ld, int64_t row0, int64_t kb, const uint64_t *Xb,
+                             int64_t kw, const int64_t *Qb, uint64_t *Lp, int64_t w_lo, int64_t w_hi, bool prep)
+{
+    if (kb <= 0 || kb > RREF_LEAF_MAX || w_lo >= w_hi) return cudaSuccess;
+    if (prep) {
+        const cudaError_t e = launch_kernel(rref_leaf_prep_kernel, dim3((int)((kb + 63) / 64)), dim3(LEAF_THREADS), 0,
+                                            st, Xb, kw, kb, Lp);
+        if (e != cudaSuccess) return e;
+    }
+    const uint64_t *Lpc = Lp;
+    return launch_kernel(rref_leaf_kernel, dim3((unsigned)((w_hi - w_lo + 1) / 2)), dim3(RLEAF_THREADS),
+                         (size_t)kb * sizeof(ulonglong2), st, A, ld, row0, kb, Lpc, Qb, w_lo, w_hi);
 }
 
 constexpr int PERM_CHUNK = 8;                          // words per CTA
@@ -396,7 +627,15 @@ __global__ void apply_moves_kernel(uint64_t *A, int64_t ld, const int64_t *moves
 
 cudaError_t setup_blocked_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(trsm_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM);
+    const int leaf_smem = (int)(TRSM_LEAF_MAX * sizeof(ulonglong2));
+    cudaError_t e = cudaFuncSetAttribute(trsm_leaf_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(trsm_leaf_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(trsm_leaf_kernel<LEAF_RPT_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rref_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(RREF_LEAF_MAX * sizeof(ulonglong2)));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(compose_moves_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)COMPOSE_MAX_SMEM);

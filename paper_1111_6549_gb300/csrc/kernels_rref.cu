@@ -221,4 +221,71 @@ cudaError_t launch_solve_status(cudaStream_t st, const int64_t *r_dev, const int
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Compact recovery: the reduced rows written back.  Row i < r is the
+// identity on the pivot columns (its own pivot Q[i] set, every other pivot
+// column clear) and, on the non-pivot columns, the reduced bits C[i]
+// (kwn words; compact position s holds the s-th non-pivot column).
+// npmask[w]: the non-pivot columns of word w; npstart[w]: the compact
+// position of the first of them.  Every word of rows < r is written.
+__global__ void rref_scatter_kernel(uint64_t *A, int64_t ld, int64_t W, int64_t r, const int64_t *__restrict__ Q,
+                                    const uint64_t *__restrict__ C, int64_t kwn,
+                                    const uint64_t *__restrict__ npmask, const int64_t *__restrict__ npstart)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int64_t total = r * W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / W, w = t - i * W;
+        const int64_t qi = __ldg(Q + i);
+        uint64_t word = (qi >> 6) == w ? (1ull << (qi & 63)) : 0ull;
+        const uint64_t mask = __ldg(npmask + w);
+        if (mask) {
+            const int nb = __popcll(mask);
+            const int64_t s0 = __ldg(npstart + w);
+            const uint64_t *ci = C + i * kwn;
+            const int64_t cw = s0 >> 6;
+            const int off = (int)(s0 & 63);
+            uint64_t f = ci[cw] >> off;
+            if (off && off + nb > 64) f |= ci[cw + 1] << (64 - off);
+            if (nb < 64) f &= (1ull << nb) - 1ull;
+            if (nb == 64) {
+                word = f;                                // no pivot column in this word
+            } else if (nb <= 32) {
+                // deposit the bits of f, lowest first, at the set positions of mask
+                uint64_t m2 = mask;
+                while (m2) {
+                    const uint64_t low = m2 & (~m2 + 1ull);
+                    if (f & 1ull) word |= low;
+                    f >>= 1;
+                    m2 ^= low;
+                }
+            } else {
+                // the same by opening a zero at every clear position of mask
+                uint64_t z = ~mask;
+                while (z) {
+                    const int p = __ffsll((long long)z) - 1;
+                    const uint64_t lowp = (1ull << p) - 1ull;
+                    f = p == 63 ? (f & lowp) : ((f & lowp) | ((f >> p) << (p + 1)));
+                    z &= z - 1ull;
+                }
+                word |= f;
+            }
+        }
+        A[i * ld + w] = word;
+    }
+}
+
+cudaError_t launch_rref_scatter(cudaStream_t st, uint64_t *A, int64_t ld, int64_t W, int64_t r, const int64_t *Q,
+                                const uint64_t *C, int64_t kwn, const uint64_t *npmask, const int64_t *npstart,
+                                int num_sms)
+{
+    int64_t blocks = (r * W + 255) / 256;
+    if (blocks < 1) return cudaSuccess;
+    if (blocks > 16 * num_sms) blocks = 16 * num_sms;
+    return launch_kernel(rref_scatter_kernel, dim3((int)blocks), dim3(256), 0, st, A, ld, W, r, Q, C, kwn, npmask,
+                         npstart);
+}
+
 }  // namespace gf2

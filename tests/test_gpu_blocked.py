@@ -115,6 +115,82 @@ def test_blocked_rref_pivot_gaps(dups, rref_block):
     assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
 
 
+@pytest.mark.parametrize("leaf", [1024, 2048, 4096])
+@pytest.mark.parametrize("kind,m,n,block", [("dense", 9000, 9000, 8192), ("lowrank", 9100, 9000, 8192),
+                                            ("dense", 8800, 12345, 4096), ("sparse", 5000, 5100, 4352)])
+def test_blocked_ple_trsm_leaf_sizes(leaf, kind, m, n, block):
+    """The fused TRSM leaves at every size (GF2_OPT_TRSM_LEAF): diagonal blocks
+    of 8192 rows halved down to the leaf, blocks of fewer rows than a leaf
+    (the low-rank and sparse cases: ragged leaves), and an odd number of
+    trailing words (the last leaf CTA owns one word)."""
+    import paper_1111_6549_gb300 as g
+    h = handle(block)
+    h.set_option(g.OPT_TRSM_LEAF, leaf)
+    A = make(kind, m, n, seed=leaf + m + n)
+    assert_ple_equal(run(h, A, m, n, ld_extra=1), ref_ple(A, m, n))
+
+
+@pytest.mark.parametrize("compact,leaf", [(1, 1), (0, 1), (0, 0)])
+@pytest.mark.parametrize("kind,m,n,rref_block,dups", [
+    ("dense", 9000, 9000, 8192, ()), ("lowrank", 9000, 9500, 4096, ()), ("dense", 6000, 13000, 8192, ()),
+    ("dense", 13000, 6000, 8192, ()), ("dense", 8200, 8200, 8192, (4000, 8191, 8192)),
+    ("sparse", 5000, 7000, 2048, (100, 3000))])
+def test_rref_leaf_base_blocks(compact, leaf, kind, m, n, rref_block, dups):
+    """The RREF recovery three ways: compact (GF2_OPT_RREF_COMPACT, only the
+    non-pivot columns solved, leaves of rref_block rows), and stripe-wise with
+    each base block reduced by the fused back-substitution leaf
+    (GF2_OPT_RREF_LEAF 1) or by one table pass per stripe (0).  Full blocks of
+    8192 pivot rows, rank-deficient and wide matrices (the words past the
+    skipped pivot columns reduced by a second leaf launch), tall ones, and
+    pivot gaps from repeated columns."""
+    import paper_1111_6549_gb300 as g
+    A = make(kind, m, n, seed=m + n + rref_block + len(dups))
+    if dups:
+        U = gi.unpack(A, m, n)
+        for c in dups:
+            U[:, c] = U[:, c - 37]
+        A = gi.pack(U, A.shape[1])
+    h = handle(0, rref_block=rref_block)
+    h.set_option(g.OPT_RREF_LEAF, leaf)
+    h.set_option(g.OPT_RREF_COMPACT, compact)
+    dR = to_dev(A, gi.words_for(n) + 1)
+    Q = vec_dev(min(m, n))
+    r = h.rref(dR, m, n, Q)
+    R0 = A.copy()
+    r0, Q0 = oracle.rref(R0, m, n)
+    assert r == r0 and np.array_equal(Q.cpu().numpy()[:r0], Q0[:r0])
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+
+
+@pytest.mark.parametrize("leaf_rows", [64, 128, 1024])
+@pytest.mark.parametrize("kind,m,n", [("dense", 700, 900), ("lowrank", 900, 700), ("zerorows", 600, 600),
+                                      ("dense", 1200, 500), ("dense", 500, 1200), ("sparse", 800, 1000),
+                                      ("zero", 300, 400), ("dense", 1, 130), ("dense", 130, 1)])
+def test_rref_compact_shapes(leaf_rows, kind, m, n):
+    """The compact recovery on small shapes, with leaves of 64 (one step, so
+    every reduction goes through the products), 128 and 1024 rows: full
+    column rank (no non-pivot column: only the identity is written), the zero
+    matrix (rank 0), single rows and columns."""
+    import paper_1111_6549_gb300 as g
+    A = np.zeros((m, gi.words_for(n)), dtype=np.uint64) if kind == "zero" else make(kind, m, n, seed=m + 3 * n)
+    h = handle(0, rref_block=leaf_rows)
+    dR = to_dev(A)
+    Q = vec_dev(min(m, n))
+    r = h.rref(dR, m, n, Q)
+    R0 = A.copy()
+    r0, Q0 = oracle.rref(R0, m, n)
+    assert r == r0 and np.array_equal(Q.cpu().numpy()[:r0], Q0[:r0])
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+
+
+@pytest.mark.parametrize("bad", [0, 512, 1000, 8192, -1])
+def test_trsm_leaf_option_rejects_other_sizes(bad):
+    import paper_1111_6549_gb300 as g
+    h = g.Handle()
+    with pytest.raises(g.GF2Error):
+        h.set_option(g.OPT_TRSM_LEAF, bad)
+
+
 @pytest.mark.parametrize("block", [64, 192, 256])
 @pytest.mark.parametrize("kind,m,n", [("dense", 1000, 1500), ("lowrank", 700, 900), ("lastrow_pivot", 600, 800),
                                       ("zerocols", 800, 1000), ("dense", 1500, 700), ("duprows", 640, 640)])
