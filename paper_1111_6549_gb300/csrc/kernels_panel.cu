@@ -244,6 +244,21 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
     const int64_t cw = d->c >> 6;
     const int nS = d->nS;
     const int maxpos = d->maxpos;
+    const int64_t wr = r >> 6;                       // the word holding column r
+    // a row CTA's first row per thread: its words (the stripe word, the next
+    // word, the word holding column r) and its map entry load beside the
+    // pivot rows' words below
+    const bool rowblk = blockIdx.x >= PREP_STAGE_BLOCKS;
+    const int64_t i0 = r + (int64_t)(blockIdx.x - PREP_FIRST_ROW_BLOCK) * blockDim.x + tid;
+    uint64_t sw0 = 0, wn0 = 0, wk0 = 0;
+    int mv0 = -1;
+    if (rowblk && i0 < m) {
+        const uint64_t *row = A + i0 * ld;
+        sw0 = row[cw];
+        wn0 = nw >= 0 ? row[nw] : 0ull;
+        wk0 = wr == cw ? 0ull : row[wr];
+        if (i0 - r <= maxpos) mv0 = map[i0];
+    }
     if (tid < KS) {
         sB[0][tid] = b0;
         sB[1][tid] = b1;
@@ -251,21 +266,32 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
         sG[tid] = (tid < rbar && nw >= 0) ? A[src * ld + nw] : 0ull;
     }
     __syncthreads();
-    const int64_t wr = r >> 6;                       // the word holding column r
 
     if (blockIdx.x < PREP_STAGE_BLOCKS) {
         // staged rows: copy the whole source row (keeping the words the
         // lookups need), then fix its L region
         __shared__ uint64_t sw3[3];                  // words cw, nw and r / 64 of the row
         for (int k = blockIdx.x; k < nS; k += PREP_STAGE_BLOCKS) {   // at most one per block
-            const uint64_t *srow = A + d->S_src[k] * ld;
-            uint64_t *dst = S + (int64_t)k * ldS;
-            for (int64_t w = tid; w < W; w += blockDim.x) {
-                const uint64_t x = srow[w];
-                dst[w] = x;
-                if (w == cw) sw3[0] = x;
-                if (w == nw) sw3[1] = x;
-                if (w == wr) sw3[2] = x;
+            const uint64_t *__restrict__ srow = A + d->S_src[k] * ld;
+            uint64_t *__restrict__ dst = S + (int64_t)k * ldS;
+            // four words per thread loaded before any is stored (one round
+            // trip up to 2048 words)
+            for (int64_t wb = tid; wb < W; wb += 4 * (int64_t)blockDim.x) {
+                uint64_t x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t w = wb + (int64_t)u * blockDim.x;
+                    x[u] = w < W ? srow[w] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t w = wb + (int64_t)u * blockDim.x;
+                    if (w >= W) break;
+                    dst[w] = x[u];
+                    if (w == cw) sw3[0] = x[u];
+                    if (w == nw) sw3[1] = x[u];
+                    if (w == wr) sw3[2] = x[u];
+                }
             }
             __syncthreads();
             if (warp == 0) {
@@ -341,17 +367,26 @@ prep_kernel(uint64_t *A, int64_t m, int64_t ld, int64_t W, int s, StripeDesc *de
     }
     __syncthreads();
     const int64_t stride = (int64_t)(gridDim.x - PREP_FIRST_ROW_BLOCK) * blockDim.x;
-    for (int64_t i = r + (int64_t)(blockIdx.x - PREP_FIRST_ROW_BLOCK) * blockDim.x + tid; i < m; i += stride) {
-        if (i - r <= maxpos) {
-            const int mv = map[i];
-            if (mv >= 0 && (mv >> 8) == s) continue;       // staged row
-        }
+    for (int64_t i = i0; i < m; i += stride) {
+        // the row's words in one round trip (the first row's already loaded):
+        // the stripe word, the next word, and the word holding column r (the
+        // stripe word itself at full rank)
+        uint64_t sw, wn, wk;
+        int mv;
         uint64_t *row = A + i * ld;
-        // the row's words in one round trip: the stripe word, the next word,
-        // and the word holding column r (the stripe word itself at full rank)
-        const uint64_t sw = row[cw];
-        const uint64_t wn = nw >= 0 ? row[nw] : 0ull;
-        const uint64_t wk = wr == cw ? sw : row[wr];
+        if (i == i0) {
+            sw = sw0;
+            wn = wn0;
+            wk = wk0;
+            mv = mv0;
+        } else {
+            sw = row[cw];
+            wn = nw >= 0 ? row[nw] : 0ull;
+            wk = wr == cw ? 0ull : row[wr];
+            mv = i - r <= maxpos ? map[i] : -1;
+        }
+        if (wr == cw) wk = sw;
+        if (mv >= 0 && (mv >> 8) == s) continue;           // staged row
         uint64_t v = 0, ix = 0, g = 0;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
