@@ -235,6 +235,7 @@ template <bool WIDE>
 __device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
 {
     __shared__ const uint64_t *sGen[KS];
+    __shared__ __align__(16) uint64_t sGt[WIDE ? KS * WT : 1];   // wide form: the tile's generator words
 
     int64_t row_lo, row_hi, w_lo;
     const int64_t W = a.W;
@@ -345,8 +346,26 @@ __device__ __forceinline__ void update_pipe_body(const UpdArgs &a, uint64_t *T)
         if (tile >= NT) continue;
         const int64_t wbase = phys(tile) * TWK;
         __syncthreads();
-        if (WIDE) build_wide_tables(T, sGen, wbase, W, w_lo);
-        else build_tables(T, sGen, wbase, W);
+        if (WIDE) {
+            // the tile's words of the 64 generator rows into shared memory in
+            // one round trip (words outside [w_lo, W) as zero: their entries
+            // are never stored back), then the tables from there
+            static_assert(KS * WT == 2 * UPD_THREADS, "two generator words per thread");
+            uint64_t gv[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int e = threadIdx.x + q * UPD_THREADS, row = e / WT;
+                const int64_t word = wbase + e % WT;
+                const uint64_t *gp = sGen[row];
+                gv[q] = (gp != nullptr && word >= w_lo && word < W) ? gp[word] : 0ull;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) sGt[threadIdx.x + q * UPD_THREADS] = gv[q];
+            __syncthreads();
+            build_wide_tables_smem(T, sGt);
+        } else {
+            build_tables(T, sGen, wbase, W);
+        }
         __syncthreads();
 
         const int64_t w0 = wbase + 2 * qd;
