@@ -45,13 +45,16 @@ def work_bits(m: int, n: int, r: int) -> float:
     return m * n * r - (m + n) * r * r / 2.0 + r ** 3 / 3.0
 
 
-def bf16_peak():
-    """Measured dense bf16 TFLOP/s (burst) of this machine's GB300, for the GEMM's roofline."""
+def bf16_peak(sustained: bool = False):
+    """Measured dense bf16 TFLOP/s of this machine's GB300 for the GEMM's roofline:
+    the burst figure (a kernel timed alone) or the sustained one (a kernel
+    timed inside a long step)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["bf16_tflops"]), "measured"
+            p = json.load(fh)
+        return float(p["bf16_tflops_sustained" if sustained else "bf16_tflops"]), "measured"
     except Exception:
-        return 1900.0, "fallback"
+        return (1700.0 if sustained else 1900.0), "fallback"
 
 
 def peaks():
@@ -691,6 +694,17 @@ def run_ours(args):
     st = h.stats()
     h.set_profiling(0)
     ms = sum(a.elapsed_time(b) for a, b in ev)
+    # one more step, right after the timed ones and not counted in them, with
+    # every GEMM launch (and nothing else) bracketed by events: the dominant
+    # kernel's live roofline (bracketing them inside the timed steps cost the
+    # step about 3 ms of lost overlap)
+    h.reset_stats()
+    h.set_profiling(5)
+    work.copy_(pristine)
+    step()
+    torch.cuda.synchronize()
+    sg = h.stats()
+    h.set_profiling(0)
     r = int(rank_dev.cpu()[0])
     # diagnostic pass (not part of the timed steps): every kernel timed
     h.reset_stats()
@@ -707,14 +721,17 @@ def run_ours(args):
     W_bits = work_bits(m, n, r)
     value = world * args.steps * W_bits / (max_ms / 1e3) / 1e9
 
-    # ---- roofline of the dominant kernel (the tabulated update), measured live
+    # ---- rooflines, measured live.  The update kernel's object comes first;
+    # the dominant kernel (the largest share of the step's launch time: the
+    # own FP4 GEMM) becomes `roofline` below.
     hbm, hbm_kind = peaks()
     upd_gbs = st["update_bytes"] / (st["update_ms"] / 1e3) / 1e9 if st["update_ms"] > 0 else None
     upd_per_launch_bytes = st["update_bytes"] / max(st["update_timed_launches"], 1)
     ratio, ratio_src = update_kernel_traffic()
     traffic = ratio * upd_per_launch_bytes if ratio is not None else None
-    rp_gbs = (st["rref_pass_bytes"] / (st["rref_pass_ms"] / 1e3) / 1e9) if st["rref_pass_ms"] > 0 else None
-    roofline = {"kernel": "update_pipe_kernel (tabulated trailing update of the PLE stripes; "
+    rp_gbs = ((st["rref_pass_bytes"] / (st["rref_pass_ms"] / 1e3) / 1e9)
+              if st["rref_pass_ms"] > 0 and st["rref_pass_bytes"] > 0 else None)
+    upd_roof = {"kernel": "update_pipe_kernel (tabulated trailing update of the PLE stripes; "
                           + ("paired 64-byte tiles)" if args.paired else "wide 128-byte tiles)"),
                 "bound": "hbm", "achieved": upd_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (upd_gbs / hbm) if upd_gbs else None, "peak_kind": hbm_kind,
@@ -729,20 +746,49 @@ def run_ours(args):
                 "update_share_of_step_diagnostic": None,
                 "kernel_ms_per_step_diagnostic": {k: sd[k + "_ms"] / diag_steps
                                                   for k in ("update", "panel", "prep", "rref_prep", "rref_pass",
-                                                            "other")},
+                                                            "gemm", "other")},
                 "algorithmic_bytes_per_step_diagnostic": sd["update_bytes"] / diag_steps,
-                "rref_pass_kernel": {"achieved_gbs": rp_gbs, "frac": (rp_gbs / hbm) if rp_gbs else None,
-                                     "launches_per_step": st["rref_pass_launches"] / args.steps,
-                                     "algorithmic_bytes_per_step": st["rref_pass_bytes"] /
-                                     max(st["rref_pass_timed_launches"], 1) * st["rref_pass_launches"] /
-                                     args.steps},
+                "rref_backsub_kernel": {"kernel": "rref_leaf_kernel (fused back-substitution leaves of the "
+                                                  "compact RREF recovery); rref_pass_kernel when the "
+                                                  "stripe-wise recovery runs",
+                                        "ms_per_step_diagnostic": sd["rref_pass_ms"] / diag_steps,
+                                        "launches_per_step": st["rref_pass_launches"] / args.steps,
+                                        "achieved_gbs": rp_gbs, "frac": (rp_gbs / hbm) if rp_gbs else None,
+                                        "algorithmic_bytes_per_step": st["rref_pass_bytes"] /
+                                        max(st["rref_pass_timed_launches"], 1) * st["rref_pass_launches"] /
+                                        args.steps},
                 "note": "achieved = algorithmic bytes / CUDA-event time of every 7th update launch "
                         "of the timed steps (events on the launching stream); the per-kind breakdown "
                         "comes from a separate pass with every launch bracketed by events (the update "
-                        "runs on a side stream beside the panels); the RREF stripe passes run in their "
-                        "own kernel (rref_pass_kernel), counted apart"}
-    roofline["update_share_of_step_diagnostic"] = (roofline["kernel_ms_per_step_diagnostic"]["update"] /
+                        "runs on a side stream beside the panels); the RREF back-substitution kernels "
+                        "are counted apart (rref_backsub_kernel: the compact recovery's leaves are bound by "
+                        "shared-memory lookups, not HBM, so they report no byte rate)"}
+    upd_roof["update_share_of_step_diagnostic"] = (upd_roof["kernel_ms_per_step_diagnostic"]["update"] /
                                                    per_step_ms) if per_step_ms > 0 else None
+    g_ms, g_fl = sg["gemm_ms"], sg["gemm_flops"]
+    g_tf = g_fl / (g_ms / 1e3) / 1e12 if g_ms > 0 and g_fl > 0 else None
+    bf16s, bf16s_kind = bf16_peak(sustained=True)
+    fp4s = 6.0 * bf16s
+    roofline = {"kernel": "gemm_f4_kernel (own tcgen05 FP4 GEMM: the blocked PLE's trailing products and "
+                          "TRSM halves, the compact RREF recovery's joins)",
+                "bound": "tensor", "achieved": g_tf, "peak": fp4s, "unit": "TFLOP/s",
+                "frac": (g_tf / fp4s) if g_tf else None,
+                "peak_kind": f"{bf16s_kind} bf16 sustained x 6 (nominal FP4 13.5 / bf16 2.25 PFLOP/s)",
+                "traffic": None,
+                "traffic_source": "none for the step's launches (their DRAM bytes depend on each product's "
+                                  "shape); a 16384^3 capture is summarised in profiles/gemm_f4_kernel_16384.md",
+                "flops_per_launch": g_fl / max(sg["gemm_timed_launches"], 1),
+                "flops_per_step": sg["gemm_flops_all"],
+                "launches_per_step": sg["gemm_launches"],
+                "timed_launches": sg["gemm_timed_launches"],
+                "ms_per_step": g_ms,
+                "dominance": "largest share of the step's serialised launch time (ncu launch list, "
+                             "profiles/launches_rref_65536.md)",
+                "note": "achieved = 2 m k n / summed CUDA-event time (events on the launching stream) of "
+                        "every GEMM launch of one step of the same workload run right after the timed steps "
+                        "with only those launches bracketed (bracketing them inside the timed steps cost "
+                        "the step about 3 ms of lost overlap); the update kernel's HBM roofline is "
+                        "update_roofline"}
 
     # ---- the plain paths: (a) the same kernels one stripe after another, no
     # look-ahead; (b) the naive baseline -- one panel per launch and the
@@ -921,7 +967,7 @@ def run_ours(args):
                                          "updates as one-by-one row additions (no tables, no blocked products, "
                                          "no look-ahead)",
                            "no_lookahead_ms": plain_ms},
-                "roofline": roofline, "gemm_roofline": gemm, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+                "roofline": roofline, "update_roofline": upd_roof, "gemm_roofline": gemm, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
                 "served": served,
                 "sparse": sparse,
                 "rref_65536_ms": max_ms / args.steps if n == 65536 else None,

@@ -434,19 +434,30 @@ typedef struct gf2_stats {
     double  rref_pass_bytes;
     int64_t rref_pass_launches;
     int64_t rref_pass_timed_launches;
+    double  gemm_ms;              /* the own FP4 GEMM (gemm_f4_kernel): event time
+                                     and 2 m k n of the launches timed while
+                                     profiling (levels 1, 2, 4 and 5), all
+                                     launches, timed launches, and 2 m k n of
+                                     every launch                               */
+    double  gemm_flops;
+    int64_t gemm_launches;
+    int64_t gemm_timed_launches;
+    double  gemm_flops_all;
 } gf2_stats;
-/* Per-launch event timing: 0 off, 1 the update kernel only, 2 every kernel,
-   3 every 7th update launch (only those add to update_ms and update_bytes),
-   4 every kernel and a timeline (gf2_get_timeline).  While profiling is off
-   update_bytes counts every update launch. */
+/* Per-launch event timing: 0 off, 1 the update kernel, the RREF
+   back-substitution and the GEMM, 2 every kernel, 3 every 7th update launch
+   (only those add to update_ms and update_bytes) and the RREF
+   back-substitution, 4 every kernel and a timeline (gf2_get_timeline), 5 the
+   GEMM launches only.  While profiling is off update_bytes counts every
+   update launch.  Other levels are clamped to 0 .. 5. */
 int gf2_set_profiling(gf2_handle_t handle, int on);
 /* Read the counters (synchronises the stream to finish the event timing). */
 int gf2_get_stats(gf2_handle_t handle, gf2_stats *out);
 int gf2_reset_stats(gf2_handle_t handle);
 /* Profiling level 4: the timed launches since the last reset, in launch
    order, as (kind, start ms, end ms) triples in out (host, 3 * max_records
-   doubles); kind 0 update, 1 panel, 2 prep, 3 RREF prep, 4 other, 5 fused
-   RREF pass; times from
+   doubles); kind 0 update, 1 panel, 2 prep, 3 RREF prep, 4 other, 5 RREF
+   back-substitution (fused pass or leaf), 6 GEMM; times from
    CUDA events recorded on each launch's stream, relative to the first one.
    *count = the number of records (more than max_records: the rest are not
    written).  Synchronises the stream. */

@@ -46,7 +46,10 @@ class _Stats(ctypes.Structure):
                 ("prep_ms", ctypes.c_double), ("rref_prep_ms", ctypes.c_double),
                 ("other_ms", ctypes.c_double), ("update_timed_launches", ctypes.c_int64),
                 ("rref_pass_ms", ctypes.c_double), ("rref_pass_bytes", ctypes.c_double),
-                ("rref_pass_launches", ctypes.c_int64), ("rref_pass_timed_launches", ctypes.c_int64)]
+                ("rref_pass_launches", ctypes.c_int64), ("rref_pass_timed_launches", ctypes.c_int64),
+                ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("gemm_launches", ctypes.c_int64), ("gemm_timed_launches", ctypes.c_int64),
+                ("gemm_flops_all", ctypes.c_double)]
 
 
 class SolveJob(ctypes.Structure):
@@ -347,9 +350,10 @@ class Handle:
 
     # ---- statistics -----------------------------------------------------
     def set_profiling(self, level) -> None:
-        """0: off, 1 (or True): time the update kernel, 2: time every kernel,
-        3: time every 7th update launch (only those count in update_ms/update_bytes),
-        4: time every kernel and keep a timeline (Handle.timeline)."""
+        """0: off, 1 (or True): time the update, RREF back-substitution and GEMM
+        launches, 2: time every kernel, 3: time every 7th update launch (only those
+        count in update_ms/update_bytes) and the back-substitution, 4: time every
+        kernel and keep a timeline (Handle.timeline), 5: time the GEMM launches only."""
         _check(load().gf2_set_profiling(self._h, int(level)), "gf2_set_profiling")
 
     def stats(self) -> dict:

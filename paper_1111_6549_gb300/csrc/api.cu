@@ -47,7 +47,11 @@ struct gf2_handle {
     std::vector<cudaEvent_t> ev_free;
     struct Pending { cudaEvent_t e0, e1; int kind; };
     std::vector<Pending> ev_pending;
-    double kind_ms[6] = {0, 0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other, rref pass
+    double kind_ms[7] = {0, 0, 0, 0, 0, 0, 0};   // update, panel, prep, rref prep, other, rref pass, GEMM
+    int64_t gemm_launches = 0;     // gemm_f4_kernel launches
+    int64_t gemm_timed = 0;        // of those, timed while profiling
+    double gemm_flops = 0;         // 2 m k n of the timed launches
+    double gemm_flops_all = 0;     // 2 m k n of every launch
     int64_t rpass_launches = 0;    // fused RREF pass launches (rref_pass_kernel)
     int64_t rpass_timed = 0;
     cudaEvent_t tl_ref = nullptr;  // profiling level 4: the timeline's time origin (first timed event)
@@ -192,7 +196,7 @@ int grow(char **buf, size_t *cap, size_t need, cudaStream_t st)
         if (e_ != cudaSuccess) { cudaGetLastError(); return GF2_ECUDA; } \
     } while (0)
 
-enum { K_UPDATE = 0, K_PANEL = 1, K_PREP = 2, K_RPREP = 3, K_OTHER = 4, K_RPASS = 5 };
+enum { K_UPDATE = 0, K_PANEL = 1, K_PREP = 2, K_RPREP = 3, K_OTHER = 4, K_RPASS = 5, K_GEMM = 6 };
 
 // With profiling on, brackets one launch with a pair of events on the
 // handle's stream; the elapsed times are summed per kernel kind later.
@@ -204,9 +208,14 @@ struct Timed {
     Timed(gf2_handle *h_, int kind_, cudaStream_t st_ = nullptr, bool enable = true)
         : h(h_), kind(kind_), st(st_ ? st_ : h_->stream)
     {
-        if (!enable || h->profiling == 0 ||
-            (h->profiling != 2 && h->profiling != 4 && kind != K_UPDATE && kind != K_RPASS))
-            return;
+        // level 1: the update, RREF back-substitution and GEMM launches; 2 and
+        // 4: every launch; 3: the update and back-substitution launches
+        // (updates sampled by the caller); 5: the GEMM launches only
+        const int lv = h->profiling;
+        const bool on = lv == 2 || lv == 4 ||
+                        (lv == 1 && (kind == K_UPDATE || kind == K_RPASS || kind == K_GEMM)) ||
+                        (lv == 3 && (kind == K_UPDATE || kind == K_RPASS)) || (lv == 5 && kind == K_GEMM);
+        if (!enable || !on) return;
         e0 = take();
         if (e0) cudaEventRecord(e0, st);
     }
@@ -239,12 +248,12 @@ int launch_update_counted(gf2_handle *h, const UpdArgs &a_in, cudaStream_t st = 
     // the fused RREF passes (their own kernel) are counted and timed apart
     const bool rpass = a_in.rref_fused != 0;
     const int64_t nth = rpass ? h->rpass_launches : h->upd_launches;
-    const bool timed = h->profiling != 3 || nth % UPD_SAMPLE == 0;
+    const bool timed = h->profiling != 5 && (h->profiling != 3 || nth % UPD_SAMPLE == 0);
     Timed t(h, rpass ? K_RPASS : K_UPDATE, st, timed);
     UpdArgs a = a_in;
     if (rpass && a.bytes) a.bytes = reinterpret_cast<unsigned long long *>(h->small + SM_BYTES2);
     if (!timed) a.bytes = nullptr;
-    else if (h->profiling) (rpass ? h->rpass_timed : h->upd_timed) += 1;
+    else if (h->profiling && t.e0) (rpass ? h->rpass_timed : h->upd_timed) += 1;
     a.err = err_dev(h);
     a.wide = h->wide_update ? 1 : 0;
     a.naive = h->naive_update ? 1 : 0;
@@ -619,10 +628,10 @@ static int rref_compact(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, in
                     Timed t(h, K_RPASS);
                     CK(launch_rref_leaf(h->stream, C, kwn, ra, kb, Xb, kw, nullptr,
                                         reinterpret_cast<uint64_t *>(h->tbuf), 0, kwn, true));
+                    if (t.e0) h->rpass_timed += 1;
                 }
                 h->launches += 3;
                 h->rpass_launches += 1;
-                if (h->profiling) h->rpass_timed += 1;
                 return GF2_OK;
             }
             const int64_t mid = ra + (((kb / 2) + 63) & ~int64_t(63));
@@ -810,16 +819,16 @@ int run_rref_back(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, int64_t 
         {
             Timed t(h, K_RPASS);
             CK(launch_rref_leaf(h->stream, A, ld, ra, kb, Xb, kw, Qs + ra, Lp, a, w_end, true));
+            if (t.e0) h->rpass_timed += 1;
         }
         h->launches += 3;
         h->rpass_launches += 1;
-        if (h->profiling) h->rpass_timed += 1;
         if (w_end < W && sk < W) {
             Timed t(h, K_RPASS);
             CK(launch_rref_leaf(h->stream, A, ld, ra, kb, Xb, kw, Qs + ra, Lp, sk, W, false));
+            if (t.e0) h->rpass_timed += 1;
             h->launches += 1;
             h->rpass_launches += 1;
-            if (h->profiling) h->rpass_timed += 1;
         }
         return GF2_OK;
     };
@@ -1289,12 +1298,19 @@ static int mul_own(gf2_handle *h, uint64_t *C, int64_t ldc, const uint64_t *A, i
             const int64_t rows_p = std::max<int64_t>(rows, 256);
             if (rows_p > rows)
                 CK(cudaMemsetAsync(A4 + (size_t)rows * rowb, 0, (size_t)(rows_p - rows) * rowb, h->stream));
+            const double flops = 2.0 * (double)rows * (double)kc * (double)n;
             {
-                Timed t(h, K_OTHER);
+                Timed t(h, K_GEMM);
                 CK(launch_gemm_f4(h->stream, C + i0 * ldc, ldc, A4, rows_p, B4t, np, rows, n, kp, err_dev(h),
                                   h->num_sms));
+                if (t.e0) {
+                    h->gemm_timed += 1;
+                    h->gemm_flops += flops;
+                }
             }
             h->launches += 2;
+            h->gemm_launches += 1;
+            h->gemm_flops_all += flops;
         }
     }
     return GF2_OK;
@@ -1858,7 +1874,7 @@ int gf2_set_option(gf2_handle_t h, int option, int64_t value)
 int gf2_set_profiling(gf2_handle_t h, int on)
 {
     if (!h) return GF2_EINVAL;
-    h->profiling = on < 0 ? 0 : (on > 4 ? 4 : on);
+    h->profiling = on < 0 ? 0 : (on > 5 ? 5 : on);
     return GF2_OK;
 }
 
@@ -1906,6 +1922,11 @@ int gf2_get_stats(gf2_handle_t h, gf2_stats *out)
     unsigned long long b2 = 0;
     CK(cudaMemcpy(&b2, h->small + SM_BYTES2, 8, cudaMemcpyDeviceToHost));
     out->rref_pass_bytes = (double)b2;
+    out->gemm_ms = h->kind_ms[K_GEMM];
+    out->gemm_flops = h->gemm_flops;
+    out->gemm_launches = h->gemm_launches;
+    out->gemm_timed_launches = h->gemm_timed;
+    out->gemm_flops_all = h->gemm_flops_all;
     out->update_bytes = (double)bytes;
     out->panel_fallbacks = fb;
     return GF2_OK;
@@ -1939,6 +1960,10 @@ int gf2_reset_stats(gf2_handle_t h)
     h->upd_timed = 0;
     h->rpass_launches = 0;
     h->rpass_timed = 0;
+    h->gemm_launches = 0;
+    h->gemm_timed = 0;
+    h->gemm_flops = 0.0;
+    h->gemm_flops_all = 0.0;
     CK(cudaMemset(h->small + SM_BYTES2, 0, 8));
     for (double &x : h->kind_ms) x = 0.0;
     CK(cudaMemset(h->small + SM_FALLBACK, 0, 12));

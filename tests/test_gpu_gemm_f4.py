@@ -59,3 +59,31 @@ def test_gemm_f4_structured(h):
     A = gi.bernoulli_matrix(m, n, 5)
     h.mul(dC, to_dev(A), to_dev(eye), m, n, n)
     assert np.array_equal(to_host(dC), A)
+
+
+@pytest.mark.parametrize("level", [1, 3, 5])
+def test_gemm_stats_count_flops(level):
+    """Profiling levels 1 and 5 time every GEMM launch (5 nothing else), level
+    3 none: the statistics carry the launches, the event time and 2 m k n of
+    the timed products and of all of them."""
+    import paper_1111_6549_gb300 as g
+    hh = g.Handle()
+    hh.set_option(g.OPT_MUL_GEMM_MIN_K, 1)
+    m, k, n = 1000, 3000, 700
+    A = gi.bernoulli_matrix(m, k, 3)
+    B = gi.bernoulli_matrix(k, n, 4)
+    dC = to_dev(np.zeros((m, gi.words_for(n)), np.uint64))
+    hh.reset_stats()
+    hh.set_profiling(level)
+    hh.mul(dC, to_dev(A), to_dev(B), m, k, n)
+    st = hh.stats()
+    hh.set_profiling(0)
+    assert st["gemm_launches"] >= 1 and st["gemm_flops_all"] == 2.0 * m * k * n
+    if level in (1, 5):
+        assert st["gemm_timed_launches"] == st["gemm_launches"]
+        assert st["gemm_flops"] == 2.0 * m * k * n and st["gemm_ms"] > 0.0
+    else:
+        assert st["gemm_timed_launches"] == 0 and st["gemm_flops"] == 0.0
+    if level == 5:
+        assert st["update_timed_launches"] == 0 and st["other_ms"] == 0.0
+    assert np.array_equal(to_host(dC, gi.words_for(n)), oracle.mul(A, B, m, k, n))
