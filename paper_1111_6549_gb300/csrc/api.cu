@@ -20,6 +20,11 @@
 
 namespace gf2 {
 thread_local bool g_pdl = false;
+// kernels_rref.cu: a join of the compact recovery with at most a few non-pivot
+// columns (C1 ^= X C2 over one-word rows) and whether it fits
+bool join_narrow_fits(int64_t kwx, int64_t nnp);
+cudaError_t launch_join_narrow(cudaStream_t st, uint64_t *C1, const uint64_t *X, int64_t kwx, const uint64_t *C2,
+                               int64_t kx, int nnp, int64_t rows, int num_sms);
 }  // namespace gf2
 
 using namespace gf2;
@@ -646,7 +651,15 @@ static int rref_compact(gf2_handle *h, uint64_t *A, int64_t m, int64_t ncols, in
                 CK(launch_gather_pivbits(h->stream, A, ld, W, ra, rows, Qs + mid, kx, kwx, X, h->num_sms));
             }
             h->launches += 1;
-            rc2 = gf2_mul(h, C + ra * kwn, kwn, X, kwx, C + mid * kwn, kwn, rows, kx, nnp, 1);
+            if (kwn == 1 && join_narrow_fits(kwx, nnp)) {
+                // at most a few non-pivot columns: parities of X's rows with
+                // C2's columns, no operand expansion
+                Timed t(h, K_OTHER);
+                CK(launch_join_narrow(h->stream, C + ra, X, kwx, C + mid, kx, (int)nnp, rows, h->num_sms));
+                h->launches += 1;
+            } else {
+                rc2 = gf2_mul(h, C + ra * kwn, kwn, X, kwx, C + mid * kwn, kwn, rows, kx, nnp, 1);
+            }
             if (rc2) return rc2;
             return solve(ra, mid);
         };

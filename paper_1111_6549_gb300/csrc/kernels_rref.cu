@@ -288,4 +288,68 @@ cudaError_t launch_rref_scatter(cudaStream_t st, uint64_t *A, int64_t ld, int64_
                          npstart);
 }
 
+// ---------------------------------------------------------------------------
+constexpr int JN_MAXC = 8;                 // non-pivot columns the narrow join takes
+constexpr int JN_THREADS = 512;
+constexpr size_t JN_MAX_SMEM = 48 * 1024;  // the columns' bit vectors in shared memory
+
+static size_t join_narrow_smem(int64_t kwx, int nnp) { return (size_t)nnp * (size_t)kwx * sizeof(uint64_t); }
+
+bool join_narrow_fits(int64_t kwx, int64_t nnp)
+{
+    return nnp >= 1 && nnp <= JN_MAXC && join_narrow_smem(kwx, (int)nnp) <= JN_MAX_SMEM;
+}
+
+// A join of the compact recovery when at most JN_MAXC columns have no pivot:
+// C1 ^= X C2 with X (rows x kx bits, kwx words per row), C2 (kx rows of one
+// word, bits 0 .. nnp-1) and C1 (rows of one word).  Each CTA first turns C2
+// into nnp bit columns over its kx rows in shared memory (one ballot per 32
+// rows and column); a warp per row of X then takes, per column, the parity
+// of the row AND the column, and the row's word gets the parities.  Reads X
+// once, with no operand expansion.
+__global__ void __launch_bounds__(JN_THREADS)
+join_narrow_kernel(uint64_t *__restrict__ C1, const uint64_t *__restrict__ X, int64_t kwx,
+                   const uint64_t *__restrict__ C2, int64_t kx, int nnp, int64_t rows)
+{
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) uint64_t colv[];   // [c][w]: bit k % 64 of word k / 64 = bit c of C2[k]
+    uint32_t *colv32 = reinterpret_cast<uint32_t *>(colv);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = JN_THREADS / 32;
+    const unsigned FULL = 0xffffffffu;
+    const int64_t groups = 2 * kwx;                       // 32-row groups, whole words
+    for (int64_t g = warp; g < groups; g += NW) {
+        const int64_t k = 32 * g + lane;
+        const uint64_t v = k < kx ? C2[k] : 0ull;
+        for (int c = 0; c < nnp; ++c) {
+            const unsigned b = __ballot_sync(FULL, (unsigned)(v >> c) & 1u);
+            if (lane == 0) colv32[(int64_t)c * groups + g] = b;
+        }
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * NW + warp; i < rows; i += (int64_t)gridDim.x * NW) {
+        const uint64_t *xr = X + i * kwx;
+        uint32_t par = 0;                                 // bit c: this lane's share of column c's parity
+        for (int64_t w = lane; w < kwx; w += 32) {
+            const uint64_t xw = xr[w];
+            for (int c = 0; c < nnp; ++c) par ^= (uint32_t)(__popcll(xw & colv[(int64_t)c * kwx + w]) & 1) << c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) par ^= __shfl_xor_sync(FULL, par, o);
+        if (lane == 0 && par) C1[i] ^= (uint64_t)par;
+    }
+}
+
+cudaError_t launch_join_narrow(cudaStream_t st, uint64_t *C1, const uint64_t *X, int64_t kwx, const uint64_t *C2,
+                               int64_t kx, int nnp, int64_t rows, int num_sms)
+{
+    if (rows <= 0 || kx <= 0 || nnp <= 0) return cudaSuccess;
+    if (!join_narrow_fits(kwx, nnp)) return cudaErrorInvalidValue;
+    int64_t blocks = (rows + JN_THREADS / 32 - 1) / (JN_THREADS / 32);
+    if (blocks > 2 * num_sms) blocks = 2 * num_sms;
+    return launch_kernel(join_narrow_kernel, dim3((int)blocks), dim3(JN_THREADS), join_narrow_smem(kwx, nnp), st, C1,
+                         X, kwx, C2, kx, nnp, rows);
+}
+
 }  // namespace gf2

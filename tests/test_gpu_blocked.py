@@ -183,6 +183,33 @@ def test_rref_compact_shapes(leaf_rows, kind, m, n):
     assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
 
 
+@pytest.mark.parametrize("m,n,dups,leaf_rows", [(3000, 3000, (100, 2000, 2999), 64), (3000, 3000, (1500,), 1024),
+                                                (2600, 2600, tuple(range(300, 2600, 300)), 128),
+                                                (2600, 2600, tuple(range(300, 2600, 260)), 128),
+                                                (9000, 9000, (8999,), -1), (700, 4000, (), 256)])
+def test_rref_compact_narrow_joins(m, n, dups, leaf_rows):
+    """Compact recovery with few non-pivot columns (columns repeated from
+    earlier ones): the joins take the narrow parity path up to eight such
+    columns (the 8-column case) and the GEMM beyond (the 9-column case and the
+    wide matrix); leaves of 64 rows make every reduction a join."""
+    import paper_1111_6549_gb300 as g
+    A = make("dense", m, n, seed=m + n + len(dups))
+    if dups:
+        U = gi.unpack(A, m, n)
+        for c in dups:
+            U[:, c] = U[:, c - 37]
+        A = gi.pack(U, A.shape[1])
+    h = g.Handle()
+    h.set_option(g.OPT_RREF_BLOCK, leaf_rows)
+    dR = to_dev(A)
+    Q = vec_dev(min(m, n))
+    r = h.rref(dR, m, n, Q)
+    R0 = A.copy()
+    r0, Q0 = oracle.rref(R0, m, n)
+    assert r == r0 and np.array_equal(Q.cpu().numpy()[:r0], Q0[:r0])
+    assert np.array_equal(to_host(dR, gi.words_for(n)), R0)
+
+
 @pytest.mark.parametrize("bad", [0, 512, 1000, 8192, -1])
 def test_trsm_leaf_option_rejects_other_sizes(bad):
     import paper_1111_6549_gb300 as g
