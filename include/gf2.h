@@ -22,7 +22,11 @@
  * Asynchrony: work is enqueued on the handle's stream (gf2_set_stream; the
  * default stream otherwise).  Entry points that return a host scalar (rank,
  * solve status) synchronise that stream before returning; the _async forms
- * write the scalar to device memory instead and do not synchronise.
+ * write the scalar to device memory instead and do not synchronise at the
+ * end.  Two options make the host wait inside a call: the blocked PLE
+ * (GF2_OPT_PLE_BLOCK, from 65536 pivot columns) reads the rank once per
+ * block, and the compact RREF recovery (GF2_OPT_RREF_COMPACT, from 8192 pivot
+ * columns) reads the rank and the pivot columns once.
  *
  * Errors: every call returns GF2_OK (0) or a GF2_E* code; gf2_strerror names
  * it.  Invalid sizes or null pointers give GF2_EINVAL before any work is
@@ -87,7 +91,9 @@ int gf2_ple_async(gf2_handle_t handle, uint64_t *A, int64_t m, int64_t n, int64_
 /*
  * Reduced row echelon form, in place (Section 2, Definition "Reduced Row
  * Echelon Form"), computed as in Section 5: PLE first, then the RREF is
- * recovered from E by clearing every pivot column above its pivot.
+ * recovered from E by clearing every pivot column above its pivot (from
+ * 8192 pivot columns on, by solving only the non-pivot columns:
+ * GF2_OPT_RREF_COMPACT).
  *   A      device, overwritten with RREF(A); rows >= rank are zero.
  *   Q      device int64[min(m, n)]: pivot columns (the column rank profile,
  *          Section 2), -1 past the rank.
